@@ -1,0 +1,174 @@
+/*
+ * rrf.h -- C ABI of the GB300 (sm_103a) randomized rank-revealing factorization library.
+ *
+ * Computes A = U T V^T (Sec. 1.1, Eq. (1)) for a real m x n matrix A with m >= n, where U (m x m) and
+ * V (n x n) are orthogonal and T (m x n) is upper trapezoidal, by one of the paper's two methods:
+ *   rrf_randutv  -- blocked randUTV_basic (Algorithm 3; Sec. 4.1);
+ *   rrf_powerurv -- powerURV (Algorithm 1; Sec. 3.2).
+ *
+ * Common conventions (every entry point):
+ *  - Matrices are column-major FP64 with an explicit leading dimension (ld >= rows).  Unless an entry
+ *    point says "host", every matrix pointer is a DEVICE pointer owned by the caller.
+ *  - A is read-only.  U, T and V are written completely (every entry of the m x m, m x n and n x n
+ *    blocks).  The output buffers must not alias A or each other.
+ *  - The Gaussian matrices the methods draw (randn in Algorithms 1 and 3) come from the
+ *    counter-based Philox-4x32-10 stream (Salmon et al., SC'11) with key = (seed lo32, seed hi32).
+ *    Block t of a draw uses counter (t lo32, t hi32, step, tag) and yields column-major elements
+ *    2t and 2t+1 by the Box-Muller transform u1 = ((x0:x1 >> 11) + 1) 2^-53, u2 = (x2:x3 >> 11) 2^-53,
+ *    z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  randUTV step i (1-based) draws
+ *    (m - b(i-1)) x b with tag 1; powerURV draws n x n with step 0, tag 2.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  Device-side
+ *    entry points only enqueue work and return; results are valid once the stream reaches them.
+ *  - `workspace` is caller-owned device memory of at least the size the matching *_workspace query
+ *    returns, 256-byte aligned.  The library never allocates in the device entry points.  One
+ *    workspace must not be used by two calls that overlap on the GPU.
+ *  - Errors: argument errors are detected on the host and returned immediately (nothing is
+ *    enqueued); rrf_last_arg_error() then names the offending argument (1-based position, LAPACK
+ *    style).  Device-side conditions (Jacobi sweep cap, barrier timeout, non-finite input) are
+ *    recorded in a status word at the start of the workspace, which every device entry point
+ *    clears when it starts: rrf_workspace_status() reads the outcome of the last call.
+ */
+#ifndef RRF_H
+#define RRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RRF_API __attribute__((visibility("default")))
+#else
+#define RRF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RRF_OK = 0,
+  RRF_INVALID_ARG = 1,      /* an argument is out of range; see rrf_last_arg_error()            */
+  RRF_CUDA_ERROR = 2,       /* a CUDA runtime call failed                                        */
+  RRF_NOT_CONVERGED = 3,    /* a b x b Jacobi SVD reached its 40-sweep cap (result still written) */
+  RRF_TIMEOUT = 4,          /* a bounded device-side wait (grid or cluster barrier) gave up       */
+  RRF_NUMERICAL = 5,        /* non-finite value met                                              */
+  RRF_UNSUPPORTED = 6,      /* shape or option this build does not handle (e.g. m < n)           */
+  RRF_WORKSPACE_TOO_SMALL = 7
+} rrf_status;
+
+/* Precision of the sketch products Y = T22^T G and the power iterations (Algorithm 3). */
+enum { RRF_SKETCH_FP64 = 0, RRF_SKETCH_BF16 = 1 };
+
+/* Options; a NULL opts pointer means all defaults (FP64 sketch, no re-orthonormalization). */
+typedef struct rrf_opts {
+  int sketch_prec;   /* RRF_SKETCH_FP64 (default) or RRF_SKETCH_BF16: the sketch GEMMs take BF16 operands
+                        with FP32 accumulation on the tensor cores; everything else stays FP64.       */
+  int reorth;        /* 1: orthonormalize the sample between applications of T22 and T22^T (Sec. 2.5
+                        (ii)); forced on for the BF16 sketch.  0 follows Algorithm 3 literally.       */
+  const int* q_per_block; /* optional HOST array of length ceil(n/b): power-iteration count of each
+                        step, overriding q (e.g. a learned policy); NULL uses q everywhere.           */
+  int reserved[4];   /* must be zero */
+} rrf_opts;
+
+/* ------------------------------------------------------------------------------------------------
+ * randUTV_basic (Algorithm 3).  For step i = 1 .. min(ceil(m/b), ceil(n/b)) with I2/J2 the current
+ * b rows/columns: sketch Y = (T22^T T22)^q T22^T G, V_i from HQR_full(Y), T(:, J2 u J3) <- T V_i,
+ * V <- V V_i, U_i and R from HQR_full(T(I2 u I3, J2)), U <- U U_i, T(I2 u I3, J3) <- U_i^T T,
+ * T(I3, J2) = 0, then the SVD of R(1:b, 1:b) makes T(I2, J2) diagonal (descending, >= 0).  The last
+ * step takes the SVD of the remaining block (via HQR then SVD when it is tall, Sec. 4.2).
+ *   m, n      : rows, columns; 1 <= n <= m.
+ *   A, lda    : input (device), lda >= m.
+ *   b         : block size, 1 <= b <= 256.
+ *   q         : power-iteration count, 0 <= q <= 16.
+ *   U, ldu    : output m x m orthogonal, ldu >= m.
+ *   T, ldt    : output m x n upper trapezoidal with diagonal b x b blocks, ldt >= m.
+ *   V, ldv    : output n x n orthogonal, ldv >= n.
+ *   seed      : key of the Gaussian stream.
+ * Returns RRF_OK once all work is enqueued.
+ * ---------------------------------------------------------------------------------------------- */
+RRF_API size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
+RRF_API rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                       double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                       uint64_t seed, void* workspace, size_t ws_bytes, const rrf_opts* opts,
+                       void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * powerURV (Algorithm 1): V = randn(n, n); q times { Yh = A V; Vh = HQR_thin(Yh); Y = A^T Vh;
+ * V = HQR_thin(Y) }; Ah = A V; [U, R] = HQR_full(Ah).  For q = 0, V is the Q factor of
+ * HQR_full(G) (RURV, Sec. 3.1).  R is returned in T (entries below the diagonal exactly 0).
+ * b is the panel width of the blocked Householder QRs (1 <= b <= 256).  Other arguments as above.
+ * ---------------------------------------------------------------------------------------------- */
+RRF_API size_t rrf_powerurv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
+RRF_API rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                        double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                        uint64_t seed, void* workspace, size_t ws_bytes, const rrf_opts* opts,
+                        void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Host-buffer forms (the paper's setting, Sec. 1.3 remark: input and outputs in CPU memory).  Same
+ * arguments, but A, U, T, V are HOST pointers (pageable or pinned; leading dimensions as above).
+ * The call allocates device buffers and a workspace with cudaMallocAsync on `stream`, copies A in,
+ * factors, copies U, T, V out, frees, and returns after the stream has finished (synchronous).  The
+ * device status word is folded into the return value.
+ * ---------------------------------------------------------------------------------------------- */
+RRF_API rrf_status rrf_randutv_host(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                            double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                            uint64_t seed, const rrf_opts* opts, void* stream);
+RRF_API rrf_status rrf_powerurv_host(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                             double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                             uint64_t seed, const rrf_opts* opts, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Building blocks, exported for kernel-level testing.  All pointers are device pointers; all calls
+ * enqueue on `stream`.
+ * ---------------------------------------------------------------------------------------------- */
+
+/* G = randn(rows, cols) from the stream described above (Sec. 2.1 "standard Gaussian matrix"). */
+RRF_API rrf_status rrf_randn(int64_t rows, int64_t cols, double* G, int64_t ldg, uint64_t seed, uint32_t step,
+                     uint32_t tag, void* stream);
+
+/* FP64 GEMM C = alpha op(A) op(B) + beta C (the products of Algorithms 1 and 3), transa/transb 'N'
+ * or 'T'.  beta == 0 does not read C.  Needs rrf_gemm_workspace(m, n, k) bytes of scratch for its
+ * split-K partial sums (0 allowed when that query returns 0). */
+RRF_API size_t rrf_gemm_workspace(int64_t m, int64_t n, int64_t k);
+RRF_API rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                    int64_t ldc, void* workspace, size_t ws_bytes, void* stream);
+
+/* Householder QR of an r x w panel (Sec. 2.4, HQR), 1 <= w <= 256, r >= w.  P is overwritten with R
+ * (upper triangle) and the Householder vectors (below the diagonal, unit leading entry implicit).
+ * Also writes tau (w), the explicit vectors Y (r x w, unit diagonal, zeros above, ldy >= r) and the
+ * compact-WY factor Tf (w x w upper triangular, H_0 ... H_{w-1} = I - Y Tf Y^T).  Reflector rule:
+ * beta = -sign(alpha) ||x|| with sign(0) = +1, tau = (beta - alpha)/beta, and tau = 0 when the
+ * entries below the diagonal are all zero. */
+RRF_API size_t rrf_panel_qr_workspace(int64_t r, int64_t w);
+RRF_API rrf_status rrf_panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
+                        int64_t ldy, double* Tf, int64_t ldtf, void* workspace, size_t ws_bytes,
+                        void* stream);
+
+/* One-sided Jacobi SVD of an r x c block with r == c <= 256 (the b x b core SVD of Algorithm 3):
+ * M = Us diag(s) Vs^T, s descending and >= 0, each pair (u_k, v_k) signed so that v_k's
+ * largest-magnitude entry is positive.  Columns with s_k = 0 get u_k by Gram-Schmidt completion.
+ * The rotation rule and stopping test are those of Hestenes' method with tolerance c * 2^-53;
+ * the column pairs follow a round-robin (tournament) ordering.  Status (converged or not) goes to
+ * the workspace status word. */
+RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
+RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
+                          double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream);
+
+/* Reads the device status word of a workspace used by any call above (synchronizes `stream`).
+ * Returns RRF_OK or the first device-side condition the last call recorded. */
+RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+RRF_API const char* rrf_status_string(rrf_status s);
+
+/* 1-based position of the first invalid argument of the last call on this thread, 0 if none. */
+RRF_API int rrf_last_arg_error(void);
+
+/* Library version string (static storage). */
+RRF_API const char* rrf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RRF_H */

@@ -1,0 +1,77 @@
+// aux.cu -- small memory-bound kernels of the drivers (initialisation of U = I, V = I, T = A; block
+// copies for the in-place small products; writing D_small and the zero blocks of Algorithm 3).
+#include <algorithm>
+
+#include "rrf_internal.cuh"
+
+namespace rrf {
+namespace {
+
+enum Op { kIdentity = 0, kCopy = 1, kZero = 2, kDiag = 3, kZeroLower = 4 };
+
+__global__ void block_kernel(int op, int64_t rows, int64_t cols, const double* __restrict__ S, int64_t lds,
+                             double* __restrict__ D, int64_t ldd, const double* __restrict__ d) {
+  const int64_t total = rows * cols;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % rows, j = idx / rows;
+    double* dst = D + i + j * ldd;
+    switch (op) {
+      case kIdentity: *dst = (i == j) ? 1.0 : 0.0; break;
+      case kCopy: *dst = S[i + j * lds]; break;
+      case kZero: *dst = 0.0; break;
+      case kDiag: *dst = (i == j) ? d[i] : 0.0; break;
+      case kZeroLower: if (i > j) *dst = 0.0; break;
+    }
+  }
+}
+
+cudaError_t launch(int op, int64_t rows, int64_t cols, const double* S, int64_t lds, double* D, int64_t ldd,
+                   const double* d, cudaStream_t s) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t grid = std::min<int64_t>((total + threads - 1) / threads, (int64_t)dev_info().sms * 16);
+  block_kernel<<<(unsigned)grid, threads, 0, s>>>(op, rows, cols, S, lds, D, ldd, d);
+  return cudaGetLastError();
+}
+
+__global__ void finite_kernel(int64_t rows, int64_t cols, const double* __restrict__ X, int64_t ld, int* status) {
+  const int64_t total = rows * cols;
+  bool bad = false;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double v = X[(idx % rows) + (idx / rows) * ld];
+    bad |= !isfinite(v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, RRF_NUMERICAL);
+}
+
+}  // namespace
+
+cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {
+  return launch(kIdentity, rows, cols, nullptr, 0, X, ld, nullptr, s);
+}
+cudaError_t copy_matrix(int64_t rows, int64_t cols, const double* S, int64_t lds, double* D, int64_t ldd,
+                        cudaStream_t s) {
+  return launch(kCopy, rows, cols, S, lds, D, ldd, nullptr, s);
+}
+cudaError_t zero_matrix(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {
+  return launch(kZero, rows, cols, nullptr, 0, X, ld, nullptr, s);
+}
+cudaError_t set_diag_block(int64_t rows, int64_t cols, const double* d, double* X, int64_t ld, cudaStream_t s) {
+  return launch(kDiag, rows, cols, nullptr, 0, X, ld, d, s);
+}
+cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {
+  return launch(kZeroLower, rows, cols, nullptr, 0, X, ld, nullptr, s);
+}
+cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status, cudaStream_t s) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t grid = std::min<int64_t>((total + threads - 1) / threads, (int64_t)dev_info().sms * 8);
+  finite_kernel<<<(unsigned)grid, threads, 0, s>>>(rows, cols, X, ld, status);
+  return cudaGetLastError();
+}
+
+}  // namespace rrf

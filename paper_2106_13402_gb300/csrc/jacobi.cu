@@ -1,0 +1,327 @@
+// jacobi.cu -- one-sided (Hestenes) Jacobi SVD of the b x b core R(1:b, 1:b) of Algorithm 3 (and of
+// the last block), on one thread-block cluster.
+//
+// FP64 on GB300 runs at ~2 DFMA/clk/SM, so a single SM would need ~10 ms for a 128 x 128 SVD; the
+// cluster spreads the rows of M and of the accumulated V over CL CTAs (distributed shared memory):
+// each CTA computes its partial column norms / inner products for all pairs of one round, the
+// partials are summed in rank order through DSMEM after one cluster barrier, every CTA derives the
+// identical rotation, and applies it to its own rows.  Pairs follow the round-robin (tournament)
+// ordering, so each round rotates c/2 disjoint pairs at once.  The rotation rule and stopping test
+// are Hestenes': skip when |gamma| <= tol sqrt(alpha beta) (tol = c 2^-53), otherwise
+// zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1+t^2),
+// sn = cs t; stop after a sweep without rotations (cap 40 sweeps -> RRF_NOT_CONVERGED).
+// Outputs: sigma_k = ||m_k|| sorted descending (ties by index), u_k = m_k / sigma_k, and each pair
+// signed so the largest-magnitude entry of v_k (first on ties) is positive.  A zero sigma_k leaves
+// u_k for the Gram-Schmidt completion kernel.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "rrf_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rrf {
+namespace {
+
+constexpr int CL = 8;
+constexpr int NT = 256;
+constexpr int kMaxC = 256;
+constexpr int kMaxSweeps = 40;
+
+struct JacobiArgs {
+  int c;
+  int rp;  // rows per CTA
+  const double* M;
+  int64_t ldm;
+  double* Us;
+  int64_t ldu;
+  double* s;
+  double* Vs;
+  int64_t ldv;
+  WsHeader* hdr;
+};
+
+__device__ __forceinline__ void round_pair(int t, int k, int ne, int& p, int& q) {
+  // circle method over ne (even) players: player 0 fixed, players 1..ne-1 rotate.
+  int a, b;
+  if (k == 0) {
+    a = 0;
+    b = 1 + t % (ne - 1);
+  } else {
+    a = 1 + (t + k) % (ne - 1);
+    b = 1 + (t - k + (ne - 1)) % (ne - 1);
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
+    jacobi_kernel(const __grid_constant__ JacobiArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ double smem[];
+  const int c = a.c, rp = a.rp, ldl = rp + 1;  // local column stride (padded)
+  double* Ml = smem;                              // [c][ldl]
+  double* Vl = smem + (size_t)c * ldl;            // [c][ldl]
+  double* part = Vl + (size_t)c * ldl;            // [2][kMaxC/2][3]
+  double* nrm = part + 2 * (kMaxC / 2) * 3;       // [kMaxC] partial squared norms
+  double* vmax = nrm + kMaxC;                     // [kMaxC] partial max |v|
+  int* vidx = reinterpret_cast<int*>(vmax + kMaxC);  // [kMaxC] row of the max
+  __shared__ int s_rot;
+  __shared__ double s_sig[kMaxC];
+  __shared__ double s_sign[kMaxC];
+  __shared__ int s_rank[kMaxC];
+
+  const int tid = threadIdx.x;
+  const int r0 = rank * rp;
+  const int nloc = max(0, min(rp, c - r0));
+  // Load my rows of M; V starts as the identity.
+  for (int idx = tid; idx < c * rp; idx += NT) {
+    const int col = idx / rp, i = idx % rp;
+    const int gi = r0 + i;
+    Ml[col * ldl + i] = (i < nloc) ? a.M[gi + (int64_t)col * a.ldm] : 0.0;
+    Vl[col * ldl + i] = (i < nloc && gi == col) ? 1.0 : 0.0;
+  }
+  if (tid == 0) s_rot = 0;
+  cluster.sync();
+
+  const int ne = c + (c & 1);
+  const int npairs = ne / 2;
+  const int rounds = ne - 1;
+  const double tol = (double)c * 0x1p-53;
+  // threads per pair (power of two, <= 32)
+  int tpp = 1;
+  while (tpp * 2 * npairs <= NT && tpp < 32) tpp *= 2;
+  const int grp = tid / tpp, sub = tid % tpp;
+  const bool active = grp < npairs;
+  int par = 0;
+  int sweep = 0;
+  bool converged = false;
+  for (sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    for (int t = 0; t < rounds; ++t) {
+      int p = 0, q = 0;
+      if (active) round_pair(t, grp, ne, p, q);
+      const bool real = active && q < c;
+      // (1) partial alpha, beta, gamma over my rows.
+      double al = 0.0, be = 0.0, ga = 0.0;
+      if (real) {
+        const double* mp = Ml + p * ldl;
+        const double* mq = Ml + q * ldl;
+        for (int i = sub; i < nloc; i += tpp) {
+          const double x = mp[i], y = mq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+      }
+      for (int o = tpp / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      }
+      double* mypart = part + (size_t)par * (kMaxC / 2) * 3;
+      if (active && sub == 0) {
+        mypart[grp * 3 + 0] = al;
+        mypart[grp * 3 + 1] = be;
+        mypart[grp * 3 + 2] = ga;
+      }
+      cluster.sync();
+      // (2) totals in rank order through DSMEM; identical on every CTA.
+      if (real) {
+        double A = 0.0, B = 0.0, G = 0.0;
+        for (int rr = 0; rr < CL; ++rr) {
+          const double* rp3 = cluster.map_shared_rank(mypart, rr) + grp * 3;
+          A += rp3[0];
+          B += rp3[1];
+          G += rp3[2];
+        }
+        if (G != 0.0 && fabs(G) > tol * sqrt(A * B)) {
+          const double zeta = (B - A) / (2.0 * G);
+          const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt);
+          const double sn = cs * tt;
+          double* mp = Ml + p * ldl;
+          double* mq = Ml + q * ldl;
+          double* vp = Vl + p * ldl;
+          double* vq = Vl + q * ldl;
+          for (int i = sub; i < nloc; i += tpp) {
+            const double x = mp[i], y = mq[i];
+            mp[i] = cs * x - sn * y;
+            mq[i] = sn * x + cs * y;
+            const double u = vp[i], v = vq[i];
+            vp[i] = cs * u - sn * v;
+            vq[i] = sn * u + cs * v;
+          }
+          if (sub == 0) atomicAdd(&s_rot, 1);
+        }
+      }
+      par ^= 1;
+      __syncthreads();
+    }
+    __syncthreads();
+    converged = (s_rot == 0);
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+  }
+  if (!converged && rank == 0 && tid == 0) set_status(&a.hdr->status, RRF_NOT_CONVERGED);
+
+  // Column norms and the position of each v_k's largest-magnitude entry.
+  for (int k = tid; k < c; k += NT) {
+    double ss = 0.0, best = -1.0;
+    int bi = 0;
+    for (int i = 0; i < nloc; ++i) {
+      const double x = Ml[k * ldl + i];
+      ss = fma(x, x, ss);
+      const double av = fabs(Vl[k * ldl + i]);
+      if (av > best) {
+        best = av;
+        bi = r0 + i;
+      }
+    }
+    nrm[k] = ss;
+    vmax[k] = best;
+    vidx[k] = bi;
+  }
+  cluster.sync();
+  for (int k = tid; k < c; k += NT) {
+    double ss = 0.0, best = -1.0;
+    int bi = 0, owner = 0;
+    for (int rr = 0; rr < CL; ++rr) {
+      ss += cluster.map_shared_rank(nrm, rr)[k];
+      const double bv = cluster.map_shared_rank(vmax, rr)[k];
+      if (bv > best) {
+        best = bv;
+        bi = cluster.map_shared_rank(vidx, rr)[k];
+        owner = rr;
+      }
+    }
+    s_sig[k] = sqrt(ss);
+    // sign of v_k at its largest-magnitude entry (read from the owner's rows)
+    const int li = bi - owner * rp;
+    const double vv = cluster.map_shared_rank(Vl, owner)[k * ldl + li];
+    s_sign[k] = (vv < 0.0) ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  for (int k = tid; k < c; k += NT) {
+    int rk = 0;
+    const double sk = s_sig[k];
+    for (int j = 0; j < c; ++j) {
+      const double sj = s_sig[j];
+      rk += (sj > sk || (sj == sk && j < k)) ? 1 : 0;
+    }
+    s_rank[k] = rk;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < c * nloc; idx += NT) {
+    const int k = idx / nloc, i = idx % nloc;
+    const int dst = s_rank[k];
+    const double sg = s_sign[k], sig = s_sig[k];
+    const int gi = r0 + i;
+    a.Vs[gi + (int64_t)dst * a.ldv] = sg * Vl[k * ldl + i];
+    a.Us[gi + (int64_t)dst * a.ldu] = (sig > 0.0) ? sg * (Ml[k * ldl + i] / sig) : 0.0;
+  }
+  if (rank == 0)
+    for (int k = tid; k < c; k += NT) {
+      a.s[s_rank[k]] = s_sig[k];
+      if (s_sig[k] == 0.0) a.hdr->flags[0] = 1;
+    }
+  cluster.sync();  // keep shared memory alive until every CTA is done reading it
+}
+
+// Gram-Schmidt completion of u_k for exactly-zero singular values (two passes against the columns
+// already present, candidates e_0, e_1, ... in order).  Runs only when the Jacobi kernel flagged it.
+__global__ void __launch_bounds__(NT) complete_kernel(int c, double* Us, int64_t ldu, const double* s,
+                                                      WsHeader* hdr) {
+  if (*(volatile int*)&hdr->flags[0] == 0) return;
+  __shared__ double w[kMaxC];
+  __shared__ double red[NT / 32];
+  __shared__ double s_d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < c; ++k) {
+    if (s[k] > 0.0) continue;
+    for (int e = 0; e < c; ++e) {
+      for (int i = tid; i < c; i += NT) w[i] = (i == e) ? 1.0 : 0.0;
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j = 0; j < c; ++j) {
+          if (j == k || (j > k && s[j] == 0.0)) continue;
+          double d = 0.0;
+          for (int i = tid; i < c; i += NT) d = fma(Us[i + (int64_t)j * ldu], w[i], d);
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          if (lane == 0) red[warp] = d;
+          __syncthreads();
+          if (tid == 0) {
+            double t = 0.0;
+            for (int x = 0; x < NT / 32; ++x) t += red[x];
+            s_d = t;
+          }
+          __syncthreads();
+          const double dd = s_d;
+          for (int i = tid; i < c; i += NT) w[i] -= dd * Us[i + (int64_t)j * ldu];
+          __syncthreads();
+        }
+      }
+      double nn = 0.0;
+      for (int i = tid; i < c; i += NT) nn = fma(w[i], w[i], nn);
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      if (lane == 0) red[warp] = nn;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int x = 0; x < NT / 32; ++x) t += red[x];
+        s_d = sqrt(t);
+      }
+      __syncthreads();
+      const double norm = s_d;
+      if (norm > 0.5) {
+        for (int i = tid; i < c; i += NT) Us[i + (int64_t)k * ldu] = w[i] / norm;
+        __syncthreads();
+        break;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) hdr->flags[0] = 0;
+}
+
+size_t jacobi_smem(int c) {
+  const int rp = (c + CL - 1) / CL;
+  return ((size_t)2 * c * (rp + 1) + 2 * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
+         kMaxC * sizeof(int);
+}
+
+}  // namespace
+
+cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
+                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream) {
+  if (c <= 0) return cudaSuccess;
+  if (c > kMaxC) return cudaErrorInvalidValue;
+  JacobiArgs a;
+  a.c = (int)c;
+  a.rp = (int)((c + CL - 1) / CL);
+  a.M = M;
+  a.ldm = ldm;
+  a.Us = Us;
+  a.ldu = ldu;
+  a.s = s;
+  a.Vs = Vs;
+  a.ldv = ldv;
+  a.hdr = hdr;
+  const size_t smem = jacobi_smem((int)c);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxC));
+    attr = true;
+  }
+  cudaError_t e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  jacobi_kernel<<<CL, NT, smem, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  complete_kernel<<<1, NT, 0, stream>>>((int)c, Us, ldu, s, hdr);
+  return cudaGetLastError();
+}
+
+}  // namespace rrf

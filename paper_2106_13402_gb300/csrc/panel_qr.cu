@@ -1,0 +1,305 @@
+// panel_qr.cu -- Householder QR of a tall r x w panel (HQR of Sec. 2.4) and its compact-WY factor.
+//
+// The panel is spread by rows over NB co-resident CTAs (cooperative launch).  Column j needs two
+// reductions over all rows -- sigma^2 = ||x(1:)||^2 of the column and the inner products with the
+// remaining columns -- and the classic formulation would need a second one after the reflector is
+// known (v^T P(:, k)).  Here the second is avoided: with v = (x - beta e1) / (alpha - beta),
+//     v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta),
+// so one reduction of [sigma^2, x^T P(:, j+1:w)] plus the owner's copy of row j gives every CTA the
+// reflector and all update coefficients.  One grid barrier per column.  Partial sums are added in
+// CTA order, so the result is bitwise deterministic.  Every barrier wait is bounded in time and
+// records RRF_TIMEOUT in the workspace status word instead of hanging.
+//
+// The compact-WY factor (Schreiber & Van Loan) is built from the Gram matrix S = Y^T Y by the forward
+// recurrence Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j), Tf(j, j) = tau_j.
+#include <algorithm>
+
+#include "rrf_internal.cuh"
+
+namespace rrf {
+namespace {
+
+constexpr int NT = 256;
+constexpr int kMaxW = 256;
+constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct PanelArgs {
+  int64_t r;
+  int w;
+  double* P;
+  int64_t ldp;
+  double* tau;
+  double* Y;
+  int64_t ldy;
+  double* Rout;  // optional w x w copy of R (zeros below the diagonal)
+  int64_t ldr;
+  double* partials;  // [2][nb][w]
+  double* rowbuf;    // [2][w]
+  WsHeader* hdr;
+  int nb;
+  int64_t rows_per;
+};
+
+// Bounded grid barrier.  Returns false (and records RRF_TIMEOUT) if the wait gave up.
+__device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, unsigned& gen, int* s_fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *s_fail = 0;
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&hdr->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&hdr->bar_count, 0u);
+      __threadfence();
+      atomicExch(&hdr->bar_gen, target);
+    } else {
+      const long long t0 = clock64();
+      volatile unsigned* g = &hdr->bar_gen;
+      while (*g != target) {
+        if (clock64() - t0 > kBarrierCycles) {
+          set_status(&hdr->status, RRF_TIMEOUT);
+          *s_fail = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    gen = target;
+    __threadfence();
+    if (*(volatile int*)&hdr->status == RRF_TIMEOUT) *s_fail = 1;
+  }
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Partial sums of column j over this CTA's rows: slot j = sum_{i>j} x_i^2, slot k>j = sum_{i>=j} x_i P(i,k).
+__device__ void column_partials(const PanelArgs& a, int j, int64_t i0, int64_t i1, double* xs,
+                                double* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t i = i0 + tid; i < i1; i += NT) xs[i - i0] = (i >= j) ? a.P[i + (int64_t)j * a.ldp] : 0.0;
+  __syncthreads();
+  for (int k = j + warp; k < a.w; k += NT / 32) {
+    double acc = 0.0;
+    if (k == j) {
+      for (int64_t i = i0 + lane; i < i1; i += 32)
+        if (i > j) acc = fma(xs[i - i0], xs[i - i0], acc);
+    } else {
+      const double* pk = a.P + (int64_t)k * a.ldp;
+      for (int64_t i = i0 + lane; i < i1; i += 32)
+        if (i >= j) acc = fma(xs[i - i0], pk[i], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[k] = acc;
+  }
+  // The owner of row j publishes P(j, j:w).
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ PanelArgs a) {
+  extern __shared__ double smem[];
+  __shared__ double red[kMaxW];
+  __shared__ double zk[kMaxW];
+  __shared__ double s_scalars[4];  // tau, beta, scal
+  __shared__ int s_fail;
+  double* xs = smem;                  // rows_per
+  double* vs = smem + a.rows_per;     // rows_per
+  const int tid = threadIdx.x;
+  const int cta = blockIdx.x;
+  const int64_t i0 = std::min<int64_t>((int64_t)cta * a.rows_per, a.r);
+  const int64_t i1 = std::min<int64_t>(i0 + a.rows_per, a.r);
+  const int w = a.w;
+  unsigned gen = 0;
+  if (tid == 0) gen = *(volatile unsigned*)&a.hdr->bar_gen;
+
+  // Phase 0: partials of column 0.
+  {
+    double* out = a.partials + ((int64_t)0 * a.nb + cta) * w;
+    column_partials(a, 0, i0, i1, xs, out);
+    if (0 >= i0 && 0 < i1)
+      for (int k = tid; k < w; k += NT) a.rowbuf[k] = a.P[(int64_t)k * a.ldp];
+  }
+  if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
+
+  for (int j = 0; j < w; ++j) {
+    const int par = j & 1;
+    // Reduce the partial sums (CTA order) and read the owner's row j.
+    const double* part = a.partials + (int64_t)par * a.nb * w;
+    const double* row = a.rowbuf + (int64_t)par * w;
+    for (int k = j + tid; k < w; k += NT) {
+      double s = 0.0;
+      for (int c = 0; c < a.nb; ++c) s += __ldcg(part + (int64_t)c * w + k);
+      red[k] = s;
+      zk[k] = __ldcg(row + k);  // P(j, k)
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double sig2 = red[j], alpha = zk[j];
+      double tau = 0.0, beta = alpha, scal = 0.0;
+      if (sig2 != 0.0) {
+        const double nrm = sqrt(alpha * alpha + sig2);
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      s_scalars[0] = tau;
+      s_scalars[1] = beta;
+      s_scalars[2] = scal;
+      if (cta == 0) a.tau[j] = tau;
+    }
+    __syncthreads();
+    const double tau = s_scalars[0], beta = s_scalars[1], scal = s_scalars[2];
+    // z_k = v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta); stored pre-multiplied by tau.
+    for (int k = j + 1 + tid; k < w; k += NT) zk[k] = tau * ((red[k] - beta * zk[k]) * scal);
+    // v over local rows (v_j = 1); column j becomes [beta; v(1:)].
+    for (int64_t i = i0 + tid; i < i1; i += NT) {
+      double v = 0.0;
+      if (i == j) {
+        v = 1.0;
+        a.P[i + (int64_t)j * a.ldp] = beta;
+      } else if (i > j) {
+        v = (tau != 0.0) ? a.P[i + (int64_t)j * a.ldp] * scal : 0.0;
+        a.P[i + (int64_t)j * a.ldp] = v;
+      }
+      vs[i - i0] = v;
+    }
+    __syncthreads();
+    // Trailing update of the panel: P(i, k) -= tau z_k v_i for i >= j, k > j.
+    if (tau != 0.0) {
+      const int lane = tid & 31, warp = tid >> 5;
+      const int64_t ib = std::max<int64_t>(i0, j);
+      for (int k = j + 1 + warp; k < w; k += NT / 32) {
+        double* pk = a.P + (int64_t)k * a.ldp;
+        const double zz = zk[k];
+        for (int64_t i = ib + lane; i < i1; i += 32) pk[i] = fma(-zz, vs[i - i0], pk[i]);
+      }
+    }
+    __syncthreads();
+    if (j + 1 < w) {
+      double* out = a.partials + ((int64_t)((j + 1) & 1) * a.nb + cta) * w;
+      column_partials(a, j + 1, i0, i1, xs, out);
+      if ((j + 1) >= i0 && (j + 1) < i1) {
+        double* rb = a.rowbuf + (int64_t)((j + 1) & 1) * w;
+        for (int k = j + 1 + tid; k < w; k += NT) rb[k] = a.P[(j + 1) + (int64_t)k * a.ldp];
+      }
+      if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
+    }
+  }
+  // Explicit reflectors Y (unit diagonal, zeros above) and the optional clean copy of R.
+  for (int k = 0; k < w; ++k) {
+    const double* pk = a.P + (int64_t)k * a.ldp;
+    double* yk = a.Y + (int64_t)k * a.ldy;
+    for (int64_t i = i0 + tid; i < i1; i += NT) yk[i] = (i < k) ? 0.0 : (i == k ? 1.0 : pk[i]);
+    if (a.Rout != nullptr)
+      for (int64_t i = i0 + tid; i < std::min<int64_t>(i1, w); i += NT)
+        a.Rout[i + (int64_t)k * a.ldr] = (i <= k) ? pk[i] : 0.0;
+  }
+}
+
+// Forward recurrence for the compact-WY factor from S = Y^T Y (one CTA; w <= 256).
+__global__ void __launch_bounds__(NT) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
+                                                   const double* __restrict__ tau, double* Tf, int64_t ldt) {
+  __shared__ double sc[kMaxW];
+  const int p = threadIdx.x;
+  for (int j = 0; j < w; ++j) {
+    if (p < w) sc[p] = S[p + (int64_t)j * lds];
+    __syncthreads();
+    if (p < w) {
+      double v = 0.0;
+      if (p < j) {
+        double acc = 0.0;
+        for (int l = p; l < j; ++l) acc = fma(Tf[p + (int64_t)l * ldt], sc[l], acc);
+        v = -tau[j] * acc;
+      } else if (p == j) {
+        v = tau[j];
+      }
+      Tf[p + (int64_t)j * ldt] = v;
+    }
+    __syncthreads();
+  }
+}
+
+int choose_nb(int64_t r) {
+  const int sms = dev_info().sms;
+  int64_t nb = (r + 63) / 64;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nb, sms));
+}
+
+}  // namespace
+
+size_t panel_scratch_bytes(int64_t r, int64_t w) {
+  const int nb = choose_nb(r);
+  size_t bytes = align_up((size_t)2 * nb * w * sizeof(double), 256);  // partials
+  bytes += align_up((size_t)2 * w * sizeof(double), 256);              // rowbuf
+  bytes += align_up((size_t)w * w * sizeof(double), 256);              // Gram matrix
+  GemmDesc g;
+  g.M = w; g.N = w; g.K = r;
+  bytes += gemm_scratch_bytes(&g, 1);
+  return bytes;
+}
+
+cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y, int64_t ldy,
+                     double* Tf, int64_t ldtf, double* Rout, int64_t ldr, double* scratch,
+                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream) {
+  if (w <= 0 || r <= 0) return cudaSuccess;
+  if (w > kMaxW || r < w) return cudaErrorInvalidValue;
+  const int nb = choose_nb(r);
+  char* base = reinterpret_cast<char*>(scratch);
+  size_t off = 0;
+  double* partials = reinterpret_cast<double*>(base + off);
+  off += align_up((size_t)2 * nb * w * sizeof(double), 256);
+  double* rowbuf = reinterpret_cast<double*>(base + off);
+  off += align_up((size_t)2 * w * sizeof(double), 256);
+  double* gram = reinterpret_cast<double*>(base + off);
+  off += align_up((size_t)w * w * sizeof(double), 256);
+  if (off > scratch_bytes) return cudaErrorInvalidValue;
+
+  // Reset the grid barrier counter (the generation word only ever advances).
+  cudaError_t e = cudaMemsetAsync(&hdr->bar_count, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+
+  PanelArgs a;
+  a.r = r;
+  a.w = (int)w;
+  a.P = P;
+  a.ldp = ldp;
+  a.tau = tau;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.Rout = Rout;
+  a.ldr = ldr;
+  a.partials = partials;
+  a.rowbuf = rowbuf;
+  a.hdr = hdr;
+  a.nb = nb;
+  a.rows_per = (r + nb - 1) / nb;
+  const size_t dyn = (size_t)2 * a.rows_per * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (dyn > 200 * 1024) return cudaErrorInvalidValue;
+  void* args[] = {(void*)&a};
+  e = cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(nb), dim3(NT), args, dyn, stream);
+  if (e != cudaSuccess) return e;
+  if (Tf != nullptr) {
+    GemmDesc g;
+    g.M = w; g.N = w; g.K = r;
+    g.A = Y; g.lda = ldy; g.ta = 1;
+    g.B = Y; g.ldb = ldy; g.tb = 0;
+    g.C = gram; g.ldc = w;
+    e = gemm_f64(&g, 1, reinterpret_cast<double*>(base + off), scratch_bytes - off, stream);
+    if (e != cudaSuccess) return e;
+    larft_kernel<<<1, NT, 0, stream>>>((int)w, gram, w, tau, Tf, ldtf);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace rrf

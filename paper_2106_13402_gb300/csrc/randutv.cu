@@ -1,0 +1,305 @@
+// randutv.cu -- host driver of randUTV_basic (Algorithm 3) on one GPU.
+//
+// Per step i (offset o = b(i-1), trailing block T22 = T(o:, o:) of r x c):
+//   G = randn(r, b); Y = T22^T G; q times { Z = T22 Y; Y = T22^T Z }      (sketch, optionally
+//                                                                        re-orthonormalized)
+//   panel HQR of Y -> (Yv, Tv);  [T(:, o:); V(:, o:)] <- [..](I - Yv Tv Yv^T)   (compact WY)
+//   panel HQR of T(o:, o:o+b) -> (Yu, Tu, R);  T(o:, o+b:) <- (I - Yu Tu^T Yu^T) T(o:, o+b:),
+//                                              U(:, o:) <- U(:, o:)(I - Yu Tu Yu^T)
+//   Jacobi SVD of R -> (Us, D, Vs); U(:, I2) Us, V(:, J2) Vs, Us^T T(I2, J3), T(I1, J2) Vs,
+//   T(I2 u I3, J2) = [D; 0].
+// The last step (J3 empty) takes the SVD of the r x c remainder, through HQR first when r > c.
+// Everything is enqueued on the caller's stream; nothing is allocated.
+#include <algorithm>
+#include <vector>
+
+#include "rrf_internal.cuh"
+
+namespace rrf {
+
+size_t sketch_bf16_scratch_bytes(int64_t m, int64_t n, int64_t b);
+cudaError_t sketch_bf16(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, const double* G,
+                        int q, double* Y, double* Z, double* Qtmp, char* scratch, size_t scratch_bytes,
+                        double* panel_scratch, size_t panel_bytes, double* gemm_scratch,
+                        size_t gemm_bytes, WsHeader* hdr, cudaStream_t stream);
+
+namespace {
+
+struct RWs {
+  WsHeader* hdr = nullptr;
+  double *G = nullptr, *Y = nullptr, *Z = nullptr, *Yv = nullptr, *Yu = nullptr;
+  double *Xa = nullptr, *Xb = nullptr, *Xc = nullptr, *Xd = nullptr;
+  double *Wa = nullptr, *Wb = nullptr;
+  double *tauv = nullptr, *tauu = nullptr, *Tv = nullptr, *Tu = nullptr, *Rs = nullptr;
+  double *Us = nullptr, *Vs = nullptr, *sig = nullptr, *Qt = nullptr;
+  double* panel = nullptr;
+  size_t panel_bytes = 0;
+  double* gemm = nullptr;
+  size_t gemm_bytes = 0;
+  char* bf16 = nullptr;
+  size_t bf16_bytes = 0;
+};
+
+size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, Arena& ar, RWs& w) {
+  const int64_t mx = std::max(m, n);
+  w.hdr = reinterpret_cast<WsHeader*>(ar.take<char>(kHeaderBytes));
+  w.G = ar.take<double>(m * b);
+  w.Y = ar.take<double>(n * b);
+  w.Z = ar.take<double>(m * b);
+  w.Yv = ar.take<double>(n * b);
+  w.Yu = ar.take<double>(m * b);
+  w.Xa = ar.take<double>(mx * b);
+  w.Xb = ar.take<double>(mx * b);
+  w.Xc = ar.take<double>(mx * b);
+  w.Xd = ar.take<double>(mx * b);
+  w.Wa = ar.take<double>(b * mx);
+  w.Wb = ar.take<double>(b * mx);
+  w.Qt = ar.take<double>(mx * b);
+  w.tauv = ar.take<double>(b);
+  w.tauu = ar.take<double>(b);
+  w.Tv = ar.take<double>(b * b);
+  w.Tu = ar.take<double>(b * b);
+  w.Rs = ar.take<double>(b * b);
+  w.Us = ar.take<double>(b * b);
+  w.Vs = ar.take<double>(b * b);
+  w.sig = ar.take<double>(b);
+  w.panel_bytes = panel_scratch_bytes(mx, b);
+  w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
+  w.gemm_bytes = (size_t)16 * mx * b * sizeof(double);
+  w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
+  if (bf16) {
+    w.bf16_bytes = sketch_bf16_scratch_bytes(m, n, b);
+    w.bf16 = ar.take<char>(w.bf16_bytes);
+  }
+  return ar.off;
+}
+
+GemmDesc gd(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, int ta, const double* B,
+            int64_t ldb, int tb, double* C, int64_t ldc, double alpha = 1.0, double beta = 0.0) {
+  GemmDesc g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.ta = ta;
+  g.B = B; g.ldb = ldb; g.tb = tb;
+  g.C = C; g.ldc = ldc;
+  g.alpha = alpha; g.beta = beta;
+  return g;
+}
+
+// Thin explicit Q (rows x k) of a panel factored by panel_qr: Q = [I; 0] - Yr (Tr Yr(0:k,:)^T).
+cudaError_t explicit_q(int64_t rows, int64_t k, const double* Yr, const double* Tr, double* Wkk, double* Q,
+                       const RWs& w, cudaStream_t s) {
+  GemmDesc g1 = gd(k, k, k, Tr, k, 0, Yr, rows, 1, Wkk, k);
+  cudaError_t e = gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s);
+  if (e != cudaSuccess) return e;
+  e = fill_identity(rows, k, Q, rows, s);
+  if (e != cudaSuccess) return e;
+  GemmDesc g2 = gd(rows, k, k, Yr, rows, 0, Wkk, k, 0, Q, rows, -1.0, 1.0);
+  return gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s);
+}
+
+// Sketch Y = (T22^T T22)^q T22^T G in FP64; with reorth, the sample is orthonormalized before
+// every application of T22 and of T22^T (Sec. 2.5 (ii)).
+cudaError_t sketch_fp64(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, int q, bool reorth,
+                        const RWs& w, cudaStream_t s) {
+  GemmDesc g = gd(c, b, r, T22, ldt, 1, w.G, r, 0, w.Y, c);
+  cudaError_t e = gemm_f64(&g, 1, w.gemm, w.gemm_bytes, s);
+  for (int j = 0; j < q && e == cudaSuccess; ++j) {
+    const double* yin = w.Y;
+    if (reorth) {
+      e = panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+      if (e == cudaSuccess) e = explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s);
+      yin = w.Qt;
+    }
+    if (e != cudaSuccess) break;
+    GemmDesc gz = gd(r, b, c, T22, ldt, 0, yin, c, 0, w.Z, r);
+    e = gemm_f64(&gz, 1, w.gemm, w.gemm_bytes, s);
+    const double* zin = w.Z;
+    if (reorth && e == cudaSuccess) {
+      e = panel_qr(r, b, w.Z, r, w.tauu, w.Yu, r, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+      if (e == cudaSuccess) e = explicit_q(r, b, w.Yu, w.Tu, w.Rs, w.Qt, w, s);
+      zin = w.Qt;
+    }
+    if (e != cudaSuccess) break;
+    GemmDesc gy = gd(c, b, r, T22, ldt, 1, zin, r, 0, w.Y, c);
+    e = gemm_f64(&gy, 1, w.gemm, w.gemm_bytes, s);
+  }
+  return e;
+}
+
+rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, double* U,
+                      int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, const rrf_opts* opts) {
+  clear_arg_error();
+  if (m < 1) { set_arg_error(1); return RRF_INVALID_ARG; }
+  if (n < 1) { set_arg_error(2); return RRF_INVALID_ARG; }
+  if (m < n) { set_arg_error(1); return RRF_UNSUPPORTED; }
+  if (A == nullptr) { set_arg_error(3); return RRF_INVALID_ARG; }
+  if (lda < m) { set_arg_error(4); return RRF_INVALID_ARG; }
+  if (b < 1 || b > 256) { set_arg_error(5); return RRF_INVALID_ARG; }
+  if (q < 0 || q > 16) { set_arg_error(6); return RRF_INVALID_ARG; }
+  if (U == nullptr) { set_arg_error(7); return RRF_INVALID_ARG; }
+  if (ldu < m) { set_arg_error(8); return RRF_INVALID_ARG; }
+  if (T == nullptr) { set_arg_error(9); return RRF_INVALID_ARG; }
+  if (ldt < m) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (V == nullptr) { set_arg_error(11); return RRF_INVALID_ARG; }
+  if (ldv < n) { set_arg_error(12); return RRF_INVALID_ARG; }
+  if (opts != nullptr) {
+    if (opts->sketch_prec != RRF_SKETCH_FP64 && opts->sketch_prec != RRF_SKETCH_BF16) {
+      set_arg_error(16); return RRF_INVALID_ARG;
+    }
+    for (int i = 0; i < 4; ++i)
+      if (opts->reserved[i] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->q_per_block != nullptr) {
+      const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
+      for (int64_t i = 0; i < steps; ++i)
+        if (opts->q_per_block[i] < 0 || opts->q_per_block[i] > 16) { set_arg_error(16); return RRF_INVALID_ARG; }
+    }
+  }
+  return RRF_OK;
+}
+
+}  // namespace
+}  // namespace rrf
+
+using namespace rrf;
+
+extern "C" size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts) {
+  if (m < 1 || n < 1 || b < 1) return 0;
+  Arena ar;
+  RWs w;
+  const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;
+  return layout(m, n, b, bf16, ar, w);
+}
+
+extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                                  double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                                  uint64_t seed, void* workspace, size_t ws_bytes, const rrf_opts* opts,
+                                  void* stream_) {
+  rrf_status st = check_args(m, n, A, lda, b, q, U, ldu, T, ldt, V, ldv, opts);
+  if (st != RRF_OK) return st;
+  const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;
+  const bool reorth = bf16 || (opts != nullptr && opts->reorth != 0);
+  const size_t need = rrf_randutv_workspace(m, n, b, opts);
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
+    set_arg_error(14);
+    return RRF_INVALID_ARG;
+  }
+  if (ws_bytes < need) {
+    set_arg_error(15);
+    return RRF_WORKSPACE_TOO_SMALL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  Arena ar;
+  ar.base = reinterpret_cast<char*>(workspace);
+  ar.cap = ws_bytes;
+  RWs w;
+  layout(m, n, b, bf16, ar, w);
+  if (ar.overflow) return RRF_WORKSPACE_TOO_SMALL;
+
+  RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
+  RRF_CUDA_TRY(check_finite(m, n, A, lda, &w.hdr->status, s));
+  // T = A; U = I_m; V = I_n.
+  RRF_CUDA_TRY(copy_matrix(m, n, A, lda, T, ldt, s));
+  RRF_CUDA_TRY(fill_identity(m, m, U, ldu, s));
+  RRF_CUDA_TRY(fill_identity(n, n, V, ldv, s));
+
+  const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
+  for (int64_t i = 1; i <= steps; ++i) {
+    const int64_t o = b * (i - 1);
+    const int64_t r = m - o, c = n - o;
+    double* T22 = T + o + o * ldt;
+    if (b * i < m && b * i < n) {
+      const int qi = (opts != nullptr && opts->q_per_block != nullptr) ? opts->q_per_block[i - 1] : q;
+      // Sketch.
+      RRF_CUDA_TRY(randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s));
+      if (bf16) {
+        RRF_CUDA_TRY(sketch_bf16(r, c, b, T22, ldt, w.G, qi, w.Y, w.Z, w.Qt, w.bf16, w.bf16_bytes, w.panel,
+                                 w.panel_bytes, w.gemm, w.gemm_bytes, w.hdr, s));
+      } else {
+        RRF_CUDA_TRY(sketch_fp64(r, c, b, T22, ldt, qi, reorth, w, s));
+      }
+      // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
+      RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,
+                            w.hdr, s));
+      {
+        double* CT = T + o * ldt;
+        double* CV = V + o * ldv;
+        GemmDesc g1[2] = {gd(m, b, c, CT, ldt, 0, w.Yv, c, 0, w.Xa, m),
+                          gd(n, b, c, CV, ldv, 0, w.Yv, c, 0, w.Xb, n)};
+        RRF_CUDA_TRY(gemm_f64(g1, 2, w.gemm, w.gemm_bytes, s));
+        GemmDesc g2[2] = {gd(m, b, b, w.Xa, m, 0, w.Tv, b, 0, w.Xc, m),
+                          gd(n, b, b, w.Xb, n, 0, w.Tv, b, 0, w.Xd, n)};
+        RRF_CUDA_TRY(gemm_f64(g2, 2, w.gemm, w.gemm_bytes, s));
+        GemmDesc g3[2] = {gd(m, c, b, w.Xc, m, 0, w.Yv, c, 1, CT, ldt, -1.0, 1.0),
+                          gd(n, c, b, w.Xd, n, 0, w.Yv, c, 1, CV, ldv, -1.0, 1.0)};
+        RRF_CUDA_TRY(gemm_f64(g3, 2, w.gemm, w.gemm_bytes, s));
+      }
+      // [U_i, R] = HQR_full(T(o:, o:o+b)).
+      RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, w.Rs, b, w.panel, w.panel_bytes,
+                            w.hdr, s));
+      {
+        double* C = T + o + (o + b) * ldt;  // r x (c - b)
+        double* CU = U + o * ldu;           // m x r
+        const int64_t nc = c - b;
+        GemmDesc g1[2] = {gd(b, nc, r, w.Yu, r, 1, C, ldt, 0, w.Wa, b),
+                          gd(m, b, r, CU, ldu, 0, w.Yu, r, 0, w.Xa, m)};
+        RRF_CUDA_TRY(gemm_f64(g1, 2, w.gemm, w.gemm_bytes, s));
+        GemmDesc g2[2] = {gd(b, nc, b, w.Tu, b, 1, w.Wa, b, 0, w.Wb, b),
+                          gd(m, b, b, w.Xa, m, 0, w.Tu, b, 0, w.Xc, m)};
+        RRF_CUDA_TRY(gemm_f64(g2, 2, w.gemm, w.gemm_bytes, s));
+        GemmDesc g3[2] = {gd(r, nc, b, w.Yu, r, 0, w.Wb, b, 0, C, ldt, -1.0, 1.0),
+                          gd(m, r, b, w.Xc, m, 0, w.Yu, r, 1, CU, ldu, -1.0, 1.0)};
+        RRF_CUDA_TRY(gemm_f64(g3, 2, w.gemm, w.gemm_bytes, s));
+      }
+      // SVD of R and the small updates.
+      RRF_CUDA_TRY(jacobi_svd(b, w.Rs, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s));
+      {
+        const int64_t nc = c - b;
+        double* UI2 = U + o * ldu;
+        double* VJ2 = V + o * ldv;
+        double* TI2J3 = T + o + (o + b) * ldt;
+        double* TI1J2 = T + o * ldt;
+        GemmDesc g[4] = {gd(m, b, b, UI2, ldu, 0, w.Us, b, 0, w.Xa, m),
+                         gd(n, b, b, VJ2, ldv, 0, w.Vs, b, 0, w.Xb, n),
+                         gd(b, nc, b, w.Us, b, 1, TI2J3, ldt, 0, w.Wa, b),
+                         gd(o, b, b, TI1J2, ldt, 0, w.Vs, b, 0, w.Xc, std::max<int64_t>(o, 1))};
+        RRF_CUDA_TRY(gemm_f64(g, o > 0 ? 4 : 3, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(copy_matrix(m, b, w.Xa, m, UI2, ldu, s));
+        RRF_CUDA_TRY(copy_matrix(n, b, w.Xb, n, VJ2, ldv, s));
+        RRF_CUDA_TRY(copy_matrix(b, nc, w.Wa, b, TI2J3, ldt, s));
+        if (o > 0) RRF_CUDA_TRY(copy_matrix(o, b, w.Xc, o, TI1J2, ldt, s));
+        RRF_CUDA_TRY(set_diag_block(r, b, w.sig, T22, ldt, s));
+      }
+    } else {
+      // Final block: SVD of the r x c remainder (c <= b).
+      const double* M = T22;
+      int64_t ldm = ldt;
+      if (r > c) {
+        RRF_CUDA_TRY(panel_qr(r, c, T22, ldt, w.tauu, w.Yu, r, w.Tu, c, w.Rs, c, w.panel, w.panel_bytes,
+                              w.hdr, s));
+        M = w.Rs;
+        ldm = c;
+      }
+      RRF_CUDA_TRY(jacobi_svd(c, M, ldm, w.Us, c, w.sig, w.Vs, c, w.hdr, s));
+      double* CU = U + o * ldu;
+      if (r > c) {  // U(:, o:) <- U(:, o:) (I - Yu Tu Yu^T)
+        GemmDesc g1 = gd(m, c, r, CU, ldu, 0, w.Yu, r, 0, w.Xa, m);
+        RRF_CUDA_TRY(gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s));
+        GemmDesc g2 = gd(m, c, c, w.Xa, m, 0, w.Tu, c, 0, w.Xc, m);
+        RRF_CUDA_TRY(gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s));
+        GemmDesc g3 = gd(m, r, c, w.Xc, m, 0, w.Yu, r, 1, CU, ldu, -1.0, 1.0);
+        RRF_CUDA_TRY(gemm_f64(&g3, 1, w.gemm, w.gemm_bytes, s));
+      }
+      double* VJ = V + o * ldv;
+      double* TI1J = T + o * ldt;
+      GemmDesc g[3] = {gd(m, c, c, CU, ldu, 0, w.Us, c, 0, w.Xa, m),
+                       gd(n, c, c, VJ, ldv, 0, w.Vs, c, 0, w.Xb, n),
+                       gd(o, c, c, TI1J, ldt, 0, w.Vs, c, 0, w.Xc, std::max<int64_t>(o, 1))};
+      RRF_CUDA_TRY(gemm_f64(g, o > 0 ? 3 : 2, w.gemm, w.gemm_bytes, s));
+      RRF_CUDA_TRY(copy_matrix(m, c, w.Xa, m, CU, ldu, s));
+      RRF_CUDA_TRY(copy_matrix(n, c, w.Xb, n, VJ, ldv, s));
+      if (o > 0) RRF_CUDA_TRY(copy_matrix(o, c, w.Xc, o, TI1J, ldt, s));
+      RRF_CUDA_TRY(set_diag_block(r, c, w.sig, T22, ldt, s));
+    }
+  }
+  return RRF_OK;
+}

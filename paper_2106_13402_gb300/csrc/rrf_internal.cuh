@@ -1,0 +1,122 @@
+// rrf_internal.cuh -- shared declarations of the CUDA path (device kernels live in their own .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/rrf.h"
+
+namespace rrf {
+
+// ---- workspace header (first 256 bytes of every workspace) -------------------------------------
+// word 0: device status (first error wins).  Words 16..: grid-barrier counters (zeroed per call).
+constexpr size_t kHeaderBytes = 256;
+struct WsHeader {
+  int status;
+  int pad0[15];
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int pad1[14];
+  int flags[32];  // per-call scratch flags (e.g. "a zero singular value was met")
+};
+static_assert(sizeof(WsHeader) <= kHeaderBytes, "header too large");
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-owned device workspace (host-side bookkeeping only).
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  size_t cap = 0;
+  bool overflow = false;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = align_up(count * sizeof(T), 256);
+    if (base == nullptr) {  // size query
+      off += bytes;
+      return nullptr;
+    }
+    if (off + bytes > cap) {
+      overflow = true;
+      return nullptr;
+    }
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ---- per-device properties -----------------------------------------------------------------------
+struct DevInfo {
+  int sms = 0;
+  int smem_optin = 0;
+  int cc_major = 0, cc_minor = 0;
+};
+const DevInfo& dev_info();
+
+// ---- thread-local argument-error slot ------------------------------------------------------------
+void set_arg_error(int pos);
+void clear_arg_error();
+
+// ---- FP64 GEMM (gemm_f64.cu) ---------------------------------------------------------------------
+struct GemmDesc {
+  int64_t M = 0, N = 0, K = 0;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  int ta = 0;  // 1: op(A) = A^T
+  const double* B = nullptr;
+  int64_t ldb = 0;
+  int tb = 0;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+// Bytes of split-K scratch the planner may use for one batch of problems.
+size_t gemm_scratch_bytes(const GemmDesc* d, int count);
+// Enqueue up to 4 independent GEMMs as one launch (plus a reduction launch when split-K is used).
+cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scratch_bytes,
+                     cudaStream_t stream);
+
+// ---- Gaussian generator (philox.cu) --------------------------------------------------------------
+cudaError_t randn_f64(int64_t rows, int64_t cols, double* G, int64_t ldg, uint64_t seed,
+                      uint32_t step, uint32_t tag, cudaStream_t stream);
+
+// ---- Householder panel (panel_qr.cu) ---------------------------------------------------------------
+size_t panel_scratch_bytes(int64_t r, int64_t w);
+// P (r x w, ld) overwritten with R / reflectors; writes tau, explicit Y (r x w), (if Tf != null)
+// the compact-WY factor and (if Rout != null) a w x w copy of R with zeros below the diagonal.
+// hdr: workspace header (barrier words + status).
+cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
+                     int64_t ldy, double* Tf, int64_t ldtf, double* Rout, int64_t ldr, double* scratch,
+                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream);
+
+// ---- Jacobi SVD (jacobi.cu) -----------------------------------------------------------------------
+// One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.
+cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
+                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream);
+
+// ---- small kernels (aux.cu) ------------------------------------------------------------------------
+cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
+cudaError_t copy_matrix(int64_t rows, int64_t cols, const double* S, int64_t lds, double* D,
+                        int64_t ldd, cudaStream_t s);
+cudaError_t zero_matrix(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
+// X(0:rows, 0:cols) = [diag(d); 0] (d has min(rows, cols) entries)
+cudaError_t set_diag_block(int64_t rows, int64_t cols, const double* d, double* X, int64_t ld,
+                           cudaStream_t s);
+// zero the strictly lower triangle of an rows x cols block
+cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
+// status |= NUMERICAL if any entry of the block is not finite
+cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status,
+                         cudaStream_t s);
+
+}  // namespace rrf
+
+#define RRF_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return RRF_CUDA_ERROR;  \
+  } while (0)

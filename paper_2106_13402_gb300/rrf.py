@@ -1,0 +1,297 @@
+"""Thin Python binding of the C ABI in include/rrf.h (argument marshalling only).
+
+Matrices are torch float64 CUDA tensors in column-major storage: a tensor X of shape (rows, cols)
+with X.stride(0) == 1 and X.stride(1) == ld >= rows (make one with ``fortran_empty`` or convert with
+``as_fortran``).  Every computation runs in the CUDA library; if it is not built or cannot be loaded
+the calls raise, there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librrf.so")
+_lock = threading.Lock()
+_lib = None
+
+RRF_OK, RRF_INVALID_ARG, RRF_CUDA_ERROR, RRF_NOT_CONVERGED, RRF_TIMEOUT, RRF_NUMERICAL, RRF_UNSUPPORTED, \
+    RRF_WORKSPACE_TOO_SMALL = range(8)
+SKETCH_FP64, SKETCH_BF16 = 0, 1
+
+EXPORTED = [
+    "rrf_randutv_workspace", "rrf_randutv", "rrf_powerurv_workspace", "rrf_powerurv", "rrf_randutv_host",
+    "rrf_powerurv_host", "rrf_randn", "rrf_gemm_workspace", "rrf_gemm", "rrf_panel_qr_workspace", "rrf_panel_qr",
+    "rrf_jacobi_svd_workspace", "rrf_jacobi_svd", "rrf_workspace_status", "rrf_status_string",
+    "rrf_last_arg_error", "rrf_version",
+]
+
+
+class RrfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        name = lib().rrf_status_string(status).decode() if _lib is not None else str(status)
+        arg = lib().rrf_last_arg_error() if _lib is not None else 0
+        super().__init__(f"{what}: {name}" + (f" (argument {arg})" if arg else ""))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("sketch_prec", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("q_per_block", ctypes.POINTER(ctypes.c_int)), ("reserved", ctypes.c_int * 4)]
+
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load librrf.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"CUDA library {_LIB_PATH} is not built; run __graft_entry__.build()")
+            L = ctypes.CDLL(_LIB_PATH)
+            fact = [_i64, _i64, _vp, _i64, _i64, ctypes.c_int, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint64,
+                    _vp, _sz, ctypes.POINTER(Opts), _vp]
+            for name in ("rrf_randutv", "rrf_powerurv"):
+                getattr(L, name).argtypes = fact
+                getattr(L, name).restype = ctypes.c_int
+            hostf = [_i64, _i64, _vp, _i64, _i64, ctypes.c_int, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_uint64,
+                     ctypes.POINTER(Opts), _vp]
+            for name in ("rrf_randutv_host", "rrf_powerurv_host"):
+                getattr(L, name).argtypes = hostf
+                getattr(L, name).restype = ctypes.c_int
+            for name in ("rrf_randutv_workspace", "rrf_powerurv_workspace"):
+                getattr(L, name).argtypes = [_i64, _i64, _i64, ctypes.POINTER(Opts)]
+                getattr(L, name).restype = _sz
+            L.rrf_randn.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vp]
+            L.rrf_randn.restype = ctypes.c_int
+            L.rrf_gemm_workspace.argtypes = [_i64, _i64, _i64]
+            L.rrf_gemm_workspace.restype = _sz
+            L.rrf_gemm.argtypes = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
+                                   _i64, ctypes.c_double, _vp, _i64, _vp, _sz, _vp]
+            L.rrf_gemm.restype = ctypes.c_int
+            L.rrf_panel_qr_workspace.argtypes = [_i64, _i64]
+            L.rrf_panel_qr_workspace.restype = _sz
+            L.rrf_panel_qr.argtypes = [_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _sz, _vp]
+            L.rrf_panel_qr.restype = ctypes.c_int
+            L.rrf_jacobi_svd_workspace.argtypes = [_i64]
+            L.rrf_jacobi_svd_workspace.restype = _sz
+            L.rrf_jacobi_svd.argtypes = [_i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
+            L.rrf_jacobi_svd.restype = ctypes.c_int
+            L.rrf_workspace_status.argtypes = [_vp, _vp]
+            L.rrf_workspace_status.restype = ctypes.c_int
+            L.rrf_status_string.argtypes = [ctypes.c_int]
+            L.rrf_status_string.restype = ctypes.c_char_p
+            L.rrf_last_arg_error.restype = ctypes.c_int
+            L.rrf_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------------------------------------ helpers
+def _torch():
+    import torch
+    return torch
+
+
+def fortran_empty(rows: int, cols: int, device="cuda", dtype=None):
+    torch = _torch()
+    dtype = dtype or torch.float64
+    return torch.empty((cols, rows), device=device, dtype=dtype).t()
+
+
+def as_fortran(x):
+    if x.dim() == 2 and x.numel() == 0:
+        return fortran_empty(x.shape[0], x.shape[1], x.device, x.dtype)
+    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _ld(x) -> int:
+    assert x.dim() == 2, "matrix expected"
+    if x.numel() == 0:
+        return max(int(x.shape[0]), 1)
+    assert x.stride(0) == 1 and x.stride(1) >= x.shape[0], "column-major (stride (1, ld)) tensor expected"
+    return max(int(x.stride(1)), int(x.shape[0]), 1)
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(st: int, what: str):
+    if st != RRF_OK:
+        raise RrfError(st, what)
+
+
+def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None):
+    o = Opts()
+    o.sketch_prec = int(sketch_prec)
+    o.reorth = 1 if reorth else 0
+    keep = None
+    if q_per_block is not None:
+        keep = (ctypes.c_int * len(q_per_block))(*[int(v) for v in q_per_block])
+        o.q_per_block = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    o._keep = keep
+    return o
+
+
+def workspace(nbytes: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------------------------- factorizations
+def _factor(name: str, A, b: int, q: int, seed: int, opts=None, ws=None, out=None, stream=None,
+            check_status: bool = True):
+    L = lib()
+    m, n = A.shape
+    A = as_fortran(A)
+    if out is None:
+        U = fortran_empty(m, m, A.device)
+        T = fortran_empty(m, n, A.device)
+        V = fortran_empty(n, n, A.device)
+    else:
+        U, T, V = out
+    optp = ctypes.byref(opts) if opts is not None else None
+    need = getattr(L, name + "_workspace")(m, n, b, optp)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    st = getattr(L, name)(m, n, _vp(A.data_ptr()), _ld(A), b, q, _vp(U.data_ptr()), _ld(U), _vp(T.data_ptr()),
+                          _ld(T), _vp(V.data_ptr()), _ld(V), seed, _vp(ws.data_ptr()), ws.numel(), optp,
+                          _stream(stream))
+    _check(st, name)
+    if check_status:
+        _check(L.rrf_workspace_status(_vp(ws.data_ptr()), _stream(stream)), name + " (device status)")
+    return U, T, V
+
+
+def randutv(A, b: int, q: int, seed: int, opts=None, ws=None, out=None, stream=None, check_status=True):
+    """randUTV_basic (Algorithm 3) through rrf_randutv: returns (U, T, V) as column-major CUDA tensors."""
+    return _factor("rrf_randutv", A, b, q, seed, opts, ws, out, stream, check_status)
+
+
+def powerurv(A, b: int, q: int, seed: int, opts=None, ws=None, out=None, stream=None, check_status=True):
+    """powerURV (Algorithm 1) through rrf_powerurv: returns (U, R, V); b is the QR panel width."""
+    return _factor("rrf_powerurv", A, b, q, seed, opts, ws, out, stream, check_status)
+
+
+def randutv_workspace_bytes(m: int, n: int, b: int, opts=None) -> int:
+    return int(lib().rrf_randutv_workspace(m, n, b, ctypes.byref(opts) if opts is not None else None))
+
+
+def powerurv_workspace_bytes(m: int, n: int, b: int, opts=None) -> int:
+    return int(lib().rrf_powerurv_workspace(m, n, b, ctypes.byref(opts) if opts is not None else None))
+
+
+def _host_factor(name: str, A: np.ndarray, b: int, q: int, seed: int, opts=None, out=None, stream=None):
+    L = lib()
+    A = np.asfortranarray(A, dtype=np.float64)
+    m, n = A.shape
+    if out is None:
+        U = np.empty((m, m), order="F")
+        T = np.empty((m, n), order="F")
+        V = np.empty((n, n), order="F")
+    else:
+        U, T, V = out
+    optp = ctypes.byref(opts) if opts is not None else None
+    sp = _stream(stream) if stream is not None else None
+
+    def p(x):
+        return _vp(x.ctypes.data)
+
+    st = getattr(L, name)(m, n, p(A), m, b, q, p(U), m, p(T), m, p(V), n, seed, optp, sp)
+    _check(st, name)
+    return U, T, V
+
+
+def randutv_host(A, b: int, q: int, seed: int, opts=None, out=None, stream=None):
+    """rrf_randutv_host: numpy (host) in and out, device buffers managed by the library."""
+    return _host_factor("rrf_randutv_host", A, b, q, seed, opts, out, stream)
+
+
+def powerurv_host(A, b: int, q: int, seed: int, opts=None, out=None, stream=None):
+    return _host_factor("rrf_powerurv_host", A, b, q, seed, opts, out, stream)
+
+
+# ---------------------------------------------------------------------------------------- building blocks
+def randn(rows: int, cols: int, seed: int, step: int, tag: int, device="cuda", stream=None):
+    G = fortran_empty(rows, cols, device)
+    _check(lib().rrf_randn(rows, cols, _vp(G.data_ptr()), max(rows, 1), seed, step, tag, _stream(stream)),
+           "rrf_randn")
+    return G
+
+
+def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None, stream=None):
+    L = lib()
+    A = as_fortran(A)
+    B = as_fortran(B)
+    m = A.shape[1] if transa == "T" else A.shape[0]
+    k = A.shape[0] if transa == "T" else A.shape[1]
+    n = B.shape[0] if transb == "T" else B.shape[1]
+    if C is None:
+        C = fortran_empty(m, n, A.device)
+        C.zero_()
+    need = L.rrf_gemm_workspace(m, n, k)
+    ws = workspace(need, A.device) if need else None
+    st = L.rrf_gemm(transa.encode(), transb.encode(), m, n, k, alpha, _vp(A.data_ptr()), _ld(A),
+                    _vp(B.data_ptr()), _ld(B), beta, _vp(C.data_ptr()), _ld(C),
+                    _vp(ws.data_ptr()) if ws is not None else None, ws.numel() if ws is not None else 0,
+                    _stream(stream))
+    _check(st, "rrf_gemm")
+    return C
+
+
+def panel_qr(P, want_tf: bool = True, stream=None):
+    """Householder QR of a panel (in place): returns (P, tau, Y, Tf)."""
+    torch = _torch()
+    L = lib()
+    P = as_fortran(P)
+    r, w = P.shape
+    tau = torch.empty(w, dtype=torch.float64, device=P.device)
+    Y = fortran_empty(r, w, P.device)
+    Tf = fortran_empty(w, w, P.device) if want_tf else None
+    need = L.rrf_panel_qr_workspace(r, w)
+    ws = workspace(need, P.device)
+    st = L.rrf_panel_qr(r, w, _vp(P.data_ptr()), _ld(P), _vp(tau.data_ptr()), _vp(Y.data_ptr()), _ld(Y),
+                        _vp(Tf.data_ptr()) if Tf is not None else None, w, _vp(ws.data_ptr()), ws.numel(),
+                        _stream(stream))
+    _check(st, "rrf_panel_qr")
+    _check(L.rrf_workspace_status(_vp(ws.data_ptr()), _stream(stream)), "rrf_panel_qr (device status)")
+    return P, tau, Y, Tf
+
+
+def jacobi_svd(M, stream=None, check_status=True):
+    """One-sided Jacobi SVD of a c x c block: returns (Us, s, Vs, status)."""
+    torch = _torch()
+    L = lib()
+    M = as_fortran(M)
+    c = M.shape[0]
+    Us = fortran_empty(c, c, M.device)
+    Vs = fortran_empty(c, c, M.device)
+    s = torch.empty(c, dtype=torch.float64, device=M.device)
+    ws = workspace(L.rrf_jacobi_svd_workspace(c), M.device)
+    st = L.rrf_jacobi_svd(c, _vp(M.data_ptr()), _ld(M), _vp(Us.data_ptr()), c, _vp(s.data_ptr()),
+                          _vp(Vs.data_ptr()), c, _vp(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(st, "rrf_jacobi_svd")
+    dev = L.rrf_workspace_status(_vp(ws.data_ptr()), _stream(stream))
+    if check_status:
+        _check(dev, "rrf_jacobi_svd (device status)")
+    return Us, s, Vs, dev
+
+
+def version() -> str:
+    return lib().rrf_version().decode()

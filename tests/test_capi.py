@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry point that
+include/rrf.h declares, and rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_2106_13402_gb300 import rrf, testmats
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    __graft_entry__.build()
+    return rrf.lib()
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rrf_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(rrf.EXPORTED) <= set(syms)
+
+
+def test_status_strings_and_version(L):
+    assert rrf.version().startswith("rrf-gb300")
+    for code, name in enumerate(["RRF_OK", "RRF_INVALID_ARG", "RRF_CUDA_ERROR", "RRF_NOT_CONVERGED", "RRF_TIMEOUT",
+                                 "RRF_NUMERICAL", "RRF_UNSUPPORTED", "RRF_WORKSPACE_TOO_SMALL"]):
+        assert L.rrf_status_string(code).decode() == name
+
+
+def _call(L, name, m, n, lda, b, q, ldu, ldt, ldv, ws=1 << 20, nullA=False):
+    fake = ctypes.c_void_p(0x10000)  # never dereferenced: validation fails first
+    return getattr(L, name)(m, n, None if nullA else fake, lda, b, q, fake, ldu, fake, ldt, fake, ldv, 1,
+                            ctypes.c_void_p(0x100000), ws, None, None)
+
+
+@pytest.mark.parametrize("name", ["rrf_randutv", "rrf_powerurv"])
+def test_argument_validation_is_host_side(L, name):
+    # m < n: unsupported (factor A^T instead, Sec. 4 footnote)
+    assert _call(L, name, 10, 20, 10, 4, 1, 10, 10, 20) == rrf.RRF_UNSUPPORTED
+    assert L.rrf_last_arg_error() == 1
+    assert _call(L, name, 0, 0, 1, 4, 1, 1, 1, 1) == rrf.RRF_INVALID_ARG
+    assert _call(L, name, 20, 10, 20, 4, 1, 20, 20, 10, nullA=True) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 3
+    assert _call(L, name, 20, 10, 19, 4, 1, 20, 20, 10) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 4
+    assert _call(L, name, 20, 10, 20, 0, 1, 20, 20, 10) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 5
+    assert _call(L, name, 20, 10, 20, 257, 1, 20, 20, 10) == rrf.RRF_INVALID_ARG
+    assert _call(L, name, 20, 10, 20, 4, -1, 20, 20, 10) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 6
+    assert _call(L, name, 20, 10, 20, 4, 1, 19, 20, 10) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 8
+    assert _call(L, name, 20, 10, 20, 4, 1, 20, 19, 10) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 10
+    assert _call(L, name, 20, 10, 20, 4, 1, 20, 20, 9) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 12
+
+
+def test_small_entry_point_validation(L):
+    fake = ctypes.c_void_p(0x10000)
+    assert L.rrf_gemm(b"X", b"N", 2, 2, 2, 1.0, fake, 2, fake, 2, 0.0, fake, 2, None, 0, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 1
+    assert L.rrf_gemm(b"N", b"N", 4, 2, 3, 1.0, fake, 3, fake, 3, 0.0, fake, 4, None, 0, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 8
+    assert L.rrf_panel_qr(10, 11, fake, 10, fake, fake, 10, None, 0, fake, 1 << 20, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 2
+    assert L.rrf_jacobi_svd(300, fake, 300, fake, 300, fake, fake, 300, fake, 1 << 20, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_randn(-1, 2, fake, 1, 0, 0, 0, None) == rrf.RRF_INVALID_ARG
+
+
+def test_workspace_queries_grow_with_size(L):
+    a = rrf.randutv_workspace_bytes(1024, 1024, 64)
+    b = rrf.randutv_workspace_bytes(2048, 2048, 64)
+    assert 0 < a < b
+    assert rrf.powerurv_workspace_bytes(1024, 512, 64) > 0
+    assert L.rrf_randutv_workspace(0, 4, 4, None) == 0
+
+
+def test_flop_model_matches_reference_counts():
+    """The algorithmic flop model of Algorithm 3 / Algorithm 1 (per-step terms documented in testmats)."""
+    n = 8192
+    assert abs(testmats.flops_randutv(n, n, 128, 1) / 1e12 - 5.28) < 0.01
+    assert abs(testmats.flops_powerurv(n, n, 1) / 1e12 - 7.70) < 0.01
+    # single-block case: SVD-only cost terms
+    assert testmats.flops_randutv(10, 8, 16, 0) == 2 * 10 * 64 + 4 * 10 * 10 * 8 + 2 * 8 * 64
+
+
+def test_batch_shapes_are_seeded_and_in_range():
+    s1 = testmats.batch_shapes(512, 31)
+    assert s1 == testmats.batch_shapes(512, 31)
+    assert all(256 <= m <= 2048 and 128 <= n <= m for m, n in s1)
+    assert len(set(s1)) > 400
