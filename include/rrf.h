@@ -159,6 +159,19 @@ RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, doubl
  * Returns RRF_OK or the first device-side condition the last call recorded. */
 RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
 
+/* ------------------------------------------------------------------------------------------------
+ * Diagnostics (not part of the method).
+ * rrf_launch_count: number of GPU kernels this library has launched in this process so far.
+ * rrf_gemm_profile_begin: from now on, bracket every FP64 GEMM launch (including its split-K
+ *   reduction) with CUDA events on its stream, up to max_launches launches; returns 0 on success.
+ * rrf_gemm_profile_end: stop, wait for the recorded events and return the summed GEMM device time
+ *   (ms), the algorithmic flops of those launches (sum of 2 M N K over their problems) and the
+ *   number of launches timed.  Returns 0 on success.
+ * ---------------------------------------------------------------------------------------------- */
+RRF_API int64_t rrf_launch_count(void);
+RRF_API int rrf_gemm_profile_begin(int max_launches);
+RRF_API int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches);
+
 /* Human-readable name of a status code (static storage). */
 RRF_API const char* rrf_status_string(rrf_status s);
 

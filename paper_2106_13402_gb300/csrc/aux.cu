@@ -33,6 +33,7 @@ cudaError_t launch(int op, int64_t rows, int64_t cols, const double* S, int64_t 
   const int threads = 256;
   const int64_t grid = std::min<int64_t>((total + threads - 1) / threads, (int64_t)dev_info().sms * 16);
   block_kernel<<<(unsigned)grid, threads, 0, s>>>(op, rows, cols, S, lds, D, ldd, d);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -71,6 +72,7 @@ cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld
   const int threads = 256;
   const int64_t grid = std::min<int64_t>((total + threads - 1) / threads, (int64_t)dev_info().sms * 8);
   finite_kernel<<<(unsigned)grid, threads, 0, s>>>(rows, cols, X, ld, status);
+  count_launch();
   return cudaGetLastError();
 }
 

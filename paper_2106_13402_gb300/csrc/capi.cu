@@ -1,6 +1,7 @@
 // capi.cu -- the remaining C-ABI entry points: building blocks exported for testing, status helpers,
 // and the host-buffer forms of the two factorizations.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "rrf_internal.cuh"
@@ -9,7 +10,9 @@ namespace rrf {
 
 namespace {
 thread_local int g_arg_error = 0;
+std::atomic<int64_t> g_launches{0};
 }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_arg_error(int pos) { g_arg_error = pos; }
 void clear_arg_error() { g_arg_error = 0; }
 
@@ -51,6 +54,8 @@ extern "C" const char* rrf_status_string(rrf_status s) {
 }
 
 extern "C" int rrf_last_arg_error(void) { return g_arg_error; }
+
+extern "C" int64_t rrf_launch_count(void) { return g_launches.load(); }
 
 extern "C" const char* rrf_version(void) { return "rrf-gb300 0.1 (sm_103a)"; }
 

@@ -8,6 +8,8 @@
 // and thin outputs are split along K (deterministic two-pass reduction) until the units fill the
 // SMs evenly.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "rrf_internal.cuh"
 
@@ -164,6 +166,20 @@ int plan_splits(const GemmDesc& d, int sms) {
   return best;
 }
 
+// Optional instrumentation: CUDA events around each launch (diagnostics API of rrf.h).
+struct GemmProfile {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  double flops = 0.0;
+  int64_t launches = 0;
+};
+GemmProfile& prof() {
+  static GemmProfile p;
+  return p;
+}
+
 }  // namespace
 
 size_t gemm_scratch_bytes(const GemmDesc* d, int count) {
@@ -218,16 +234,64 @@ cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scrat
   if (batch.count == 0) return cudaSuccess;
   batch.total_units = units;
   batch.total_elems = elems;
+  GemmProfile& pf = prof();
+  cudaEvent_t ev_end = nullptr;
+  if (pf.on) {
+    std::lock_guard<std::mutex> lock(pf.mu);
+    if (pf.used + 2 <= pf.ev.size()) {
+      cudaEventRecord(pf.ev[pf.used], stream);
+      ev_end = pf.ev[pf.used + 1];
+      pf.used += 2;
+      for (int i = 0; i < batch.count; ++i) pf.flops += 2.0 * batch.p[i].d.M * batch.p[i].d.N * batch.p[i].d.K;
+      pf.launches += 1;
+    }
+  }
   gemm_f64_kernel<<<(unsigned)units, NT, 0, stream>>>(batch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (elems > 0) {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((elems + threads - 1) / threads, (int64_t)sms * 16);
     gemm_reduce_kernel<<<(unsigned)blocks, threads, 0, stream>>>(batch);
+    count_launch();
     e = cudaGetLastError();
   }
+  if (ev_end != nullptr) cudaEventRecord(ev_end, stream);
   return e;
 }
 
 }  // namespace rrf
+
+extern "C" int rrf_gemm_profile_begin(int max_launches) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  const size_t want = (size_t)2 * (max_launches > 0 ? max_launches : 0);
+  while (pf.ev.size() < want) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return 1;
+    pf.ev.push_back(e);
+  }
+  pf.used = 0;
+  pf.flops = 0.0;
+  pf.launches = 0;
+  pf.on = true;
+  return 0;
+}
+
+extern "C" int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  pf.on = false;
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < pf.used; i += 2) {
+    if (cudaEventSynchronize(pf.ev[i + 1]) != cudaSuccess) return 1;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]) != cudaSuccess) return 1;
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (flops) *flops = pf.flops;
+  if (launches) *launches = pf.launches;
+  return 0;
+}

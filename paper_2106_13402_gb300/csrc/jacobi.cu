@@ -318,9 +318,11 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   cudaError_t e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   jacobi_kernel<<<CL, NT, smem, stream>>>(a);
+  count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   complete_kernel<<<1, NT, 0, stream>>>((int)c, Us, ldu, s, hdr);
+  count_launch();
   return cudaGetLastError();
 }
 

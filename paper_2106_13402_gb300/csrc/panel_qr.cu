@@ -286,6 +286,7 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   }
   if (dyn > 200 * 1024) return cudaErrorInvalidValue;
   void* args[] = {(void*)&a};
+  count_launch();
   e = cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(nb), dim3(NT), args, dyn, stream);
   if (e != cudaSuccess) return e;
   if (Tf != nullptr) {
@@ -297,6 +298,7 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
     e = gemm_f64(&g, 1, reinterpret_cast<double*>(base + off), scratch_bytes - off, stream);
     if (e != cudaSuccess) return e;
     larft_kernel<<<1, NT, 0, stream>>>((int)w, gram, w, tau, Tf, ldtf);
+    count_launch();
     e = cudaGetLastError();
   }
   return e;

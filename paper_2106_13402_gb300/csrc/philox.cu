@@ -68,6 +68,7 @@ cudaError_t randn_f64(int64_t rows, int64_t cols, double* G, int64_t ldg, uint64
   const int64_t grid = std::min<int64_t>((nblocks + threads - 1) / threads, (int64_t)dev_info().sms * 32);
   randn_kernel<<<(unsigned)grid, threads, 0, stream>>>(G, rows, ldg, total, (uint32_t)seed,
                                                         (uint32_t)(seed >> 32), step, tag);
+  count_launch();
   return cudaGetLastError();
 }
 

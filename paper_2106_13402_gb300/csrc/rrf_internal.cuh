@@ -58,6 +58,9 @@ struct DevInfo {
 };
 const DevInfo& dev_info();
 
+// ---- launch accounting (every kernel launch of the library calls this once) -------------------------
+void count_launch();
+
 // ---- thread-local argument-error slot ------------------------------------------------------------
 void set_arg_error(int pos);
 void clear_arg_error();

@@ -26,7 +26,7 @@ EXPORTED = [
     "rrf_randutv_workspace", "rrf_randutv", "rrf_powerurv_workspace", "rrf_powerurv", "rrf_randutv_host",
     "rrf_powerurv_host", "rrf_randn", "rrf_gemm_workspace", "rrf_gemm", "rrf_panel_qr_workspace", "rrf_panel_qr",
     "rrf_jacobi_svd_workspace", "rrf_jacobi_svd", "rrf_workspace_status", "rrf_status_string",
-    "rrf_last_arg_error", "rrf_version",
+    "rrf_last_arg_error", "rrf_version", "rrf_launch_count", "rrf_gemm_profile_begin", "rrf_gemm_profile_end",
 ]
 
 
@@ -94,6 +94,12 @@ def lib():
             L.rrf_status_string.restype = ctypes.c_char_p
             L.rrf_last_arg_error.restype = ctypes.c_int
             L.rrf_version.restype = ctypes.c_char_p
+            L.rrf_launch_count.restype = ctypes.c_int64
+            L.rrf_gemm_profile_begin.argtypes = [ctypes.c_int]
+            L.rrf_gemm_profile_begin.restype = ctypes.c_int
+            L.rrf_gemm_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_int64)]
+            L.rrf_gemm_profile_end.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -291,6 +297,24 @@ def jacobi_svd(M, stream=None, check_status=True):
     if check_status:
         _check(dev, "rrf_jacobi_svd (device status)")
     return Us, s, Vs, dev
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process (diagnostics)."""
+    return int(lib().rrf_launch_count())
+
+
+def gemm_profile_begin(max_launches: int = 100000):
+    if lib().rrf_gemm_profile_begin(int(max_launches)) != 0:
+        raise RuntimeError("rrf_gemm_profile_begin failed")
+
+
+def gemm_profile_end():
+    """Returns (total GEMM device ms, algorithmic flops, launches) since gemm_profile_begin."""
+    ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    if lib().rrf_gemm_profile_end(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)) != 0:
+        raise RuntimeError("rrf_gemm_profile_end failed")
+    return ms.value, fl.value, n.value
 
 
 def version() -> str:

@@ -117,14 +117,17 @@ def batch_shapes(count: int, seed: int, m_lo: int = 256, m_hi: int = 2048, n_lo:
     return [(int(a), int(b)) for a, b in zip(ms, ns)]
 
 
-def flops_randutv(m: int, n: int, b: int, q: int) -> float:
+def flops_randutv(m: int, n: int, b: int, q: int, max_steps: int = 0) -> float:
     """Algorithmic flop count of randUTV_basic (Algorithm 3), FP64-equivalent.
 
     Per step i < s (r = m - b(i-1), c = n - b(i-1)): sketch (2+4q) r c b, HQR of Y 2cb^2,
     V-application 4mcb + 4ncb, panel HQR 2rb^2, U-application 4mrb + 4r(c-b)b, small updates
     2mb^2 + 2nb^2 + 2b^2(c-b) + 2(i-1)b^3; final block 2rc^2 + 4mrc + 2nc^2 + 2(i-1)bc^2.
+    max_steps > 0 counts only the first max_steps steps (a partial factorization).
     """
     steps = min(math.ceil(m / b), math.ceil(n / b))
+    if max_steps > 0:
+        steps = min(steps, max_steps)
     f = 0.0
     for i in range(1, steps + 1):
         o = b * (i - 1)
