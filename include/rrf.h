@@ -155,6 +155,21 @@ RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
 RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                           double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream);
 
+/* Householder panel QR that allocates nothing and takes no workspace.  The paper has no counterpart:
+ * this serves callers that cannot give the library device memory for scratch -- code running under
+ * a memory manager that owns the whole device, or loops that must not allocate once running.
+ * Arguments r, w, P, ldp, tau, Y, ldy are those of rrf_panel_qr (same results; no compact-WY
+ * factor).  `status`: optional DEVICE pointer to one int that receives the device status
+ * (0 = ok, RRF_TIMEOUT if a grid-barrier wait gave up).
+ * Scratch: a fixed 2 MiB array in device global memory, held by every GPU that loads the library
+ * until the process exits; w <= 256 with up to 152 cooperating CTAs fits (larger needs return
+ * RRF_UNSUPPORTED).  All calls share the array, so calls that overlap on the GPU (different
+ * streams, or threads) race and must be serialized by the caller.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating library routine. */
+RRF_API rrf_status rrf_panel_qr_noalloc(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
+                                        int64_t ldy, int* status, void* stream);
+
 /* Reads the device status word of a workspace used by any call above (synchronizes `stream`).
  * Returns RRF_OK or the first device-side condition the last call recorded. */
 RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
