@@ -134,6 +134,16 @@ RRF_API rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                     int64_t ldc, void* workspace, size_t ws_bytes, void* stream);
 
+/* BF16 x BF16 GEMM with FP32 accumulation on the tensor cores (the products of the BF16 sketch,
+ * Sec. 2.5: the range finder only needs a subspace): D = alpha A B^T, where A (m x k) and B (n x k) are
+ * stored as rows of k contiguous BF16 values (raw 16-bit patterns), leading dimensions lda, ldb in
+ * elements (multiples of 8, bases 16-byte aligned); D is FP64 column-major, ldd >= m; 1 <= n <= 256.
+ * Needs rrf_gemm_bf16_workspace(m, n, k) bytes (split-K partial sums, summed in split order). */
+RRF_API size_t rrf_gemm_bf16_workspace(int64_t m, int64_t n, int64_t k);
+RRF_API rrf_status rrf_gemm_bf16(int64_t m, int64_t n, int64_t k, double alpha, const uint16_t* A, int64_t lda,
+                                 const uint16_t* B, int64_t ldb, double* D, int64_t ldd, void* workspace,
+                                 size_t ws_bytes, void* stream);
+
 /* Householder QR of an r x w panel (Sec. 2.4, HQR), 1 <= w <= 256, r >= w.  P is overwritten with R
  * (upper triangle) and the Householder vectors (below the diagonal, unit leading entry implicit).
  * Also writes tau (w), the explicit vectors Y (r x w, unit diagonal, zeros above, ldy >= r) and the

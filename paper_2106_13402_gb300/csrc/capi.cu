@@ -109,6 +109,39 @@ extern "C" rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, i
   return RRF_OK;
 }
 
+extern "C" size_t rrf_gemm_bf16_workspace(int64_t m, int64_t n, int64_t k) {
+  if (m < 1 || n < 1) return kHeaderBytes;
+  return kHeaderBytes + tc_part_bytes(m, n, k);
+}
+
+extern "C" rrf_status rrf_gemm_bf16(int64_t m, int64_t n, int64_t k, double alpha, const uint16_t* A, int64_t lda,
+                                    const uint16_t* B, int64_t ldb, double* D, int64_t ldd, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  clear_arg_error();
+  if (m < 1) { set_arg_error(1); return RRF_INVALID_ARG; }
+  if (n < 1 || n > 256) { set_arg_error(2); return RRF_INVALID_ARG; }
+  if (k < 0) { set_arg_error(3); return RRF_INVALID_ARG; }
+  if (A == nullptr || (reinterpret_cast<uintptr_t>(A) & 15) != 0) { set_arg_error(5); return RRF_INVALID_ARG; }
+  if (lda < std::max<int64_t>(k, 1) || (lda % 8) != 0) { set_arg_error(6); return RRF_INVALID_ARG; }
+  if (B == nullptr || (reinterpret_cast<uintptr_t>(B) & 15) != 0) { set_arg_error(7); return RRF_INVALID_ARG; }
+  if (ldb < std::max<int64_t>(k, 1) || (ldb % 8) != 0) { set_arg_error(8); return RRF_INVALID_ARG; }
+  if (D == nullptr) { set_arg_error(9); return RRF_INVALID_ARG; }
+  if (ldd < m) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
+    set_arg_error(11);
+    return RRF_INVALID_ARG;
+  }
+  if (ws_bytes < rrf_gemm_bf16_workspace(m, n, k)) { set_arg_error(12); return RRF_WORKSPACE_TOO_SMALL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(workspace);
+  RRF_CUDA_TRY(cudaMemsetAsync(hdr, 0, kHeaderBytes, s));
+  RRF_CUDA_TRY(gemm_bf16_tn(m, n, k, reinterpret_cast<const __nv_bfloat16*>(A), lda,
+                            reinterpret_cast<const __nv_bfloat16*>(B), ldb, alpha, D, ldd,
+                            reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + kHeaderBytes),
+                            ws_bytes - kHeaderBytes, &hdr->status, s));
+  return RRF_OK;
+}
+
 extern "C" size_t rrf_panel_qr_workspace(int64_t r, int64_t w) {
   return kHeaderBytes + align_up(panel_scratch_bytes(r, w), 256);
 }

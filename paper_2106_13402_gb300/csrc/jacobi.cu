@@ -64,8 +64,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
   const int c = a.c, rp = a.rp, ldl = rp + 1;  // local column stride (padded)
   double* Ml = smem;                              // [c][ldl]
   double* Vl = smem + (size_t)c * ldl;            // [c][ldl]
-  double* part = Vl + (size_t)c * ldl;            // [2][kMaxC/2][3]
-  double* nrm = part + 2 * (kMaxC / 2) * 3;       // [kMaxC] partial squared norms
+  double* part = Vl + (size_t)c * ldl;            // [2][CL][kMaxC/2][3]: every CTA's partials, pushed
+  double* nrm = part + 2 * CL * (kMaxC / 2) * 3;  // [kMaxC] partial squared norms
   double* vmax = nrm + kMaxC;                     // [kMaxC] partial max |v|
   int* vidx = reinterpret_cast<int*>(vmax + kMaxC);  // [kMaxC] row of the max
   __shared__ int s_rot;
@@ -120,18 +120,24 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
         be += __shfl_xor_sync(0xffffffffu, be, o);
         ga += __shfl_xor_sync(0xffffffffu, ga, o);
       }
-      double* mypart = part + (size_t)par * (kMaxC / 2) * 3;
+      // (2) push my partials into every CTA's buffer (remote stores do not stall), one cluster
+      // barrier, then sum the local copies in rank order: identical totals on every CTA.
+      double* slot = part + ((size_t)(par * CL + rank) * (kMaxC / 2) + grp) * 3;
       if (active && sub == 0) {
-        mypart[grp * 3 + 0] = al;
-        mypart[grp * 3 + 1] = be;
-        mypart[grp * 3 + 2] = ga;
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr) {
+          double* dst = cluster.map_shared_rank(slot, rr);
+          dst[0] = al;
+          dst[1] = be;
+          dst[2] = ga;
+        }
       }
       cluster.sync();
-      // (2) totals in rank order through DSMEM; identical on every CTA.
       if (real) {
         double A = 0.0, B = 0.0, G = 0.0;
+#pragma unroll
         for (int rr = 0; rr < CL; ++rr) {
-          const double* rp3 = cluster.map_shared_rank(mypart, rr) + grp * 3;
+          const double* rp3 = part + ((size_t)(par * CL + rr) * (kMaxC / 2) + grp) * 3;
           A += rp3[0];
           B += rp3[1];
           G += rp3[2];
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(NT) complete_kernel(int c, double* Us, int64_t
 
 size_t jacobi_smem(int c) {
   const int rp = (c + CL - 1) / CL;
-  return ((size_t)2 * c * (rp + 1) + 2 * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
+  return ((size_t)2 * c * (rp + 1) + 2 * CL * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
          kMaxC * sizeof(int);
 }
 

@@ -33,11 +33,12 @@ struct PanelArgs {
   int64_t ldy;
   double* Rout;  // optional w x w copy of R (zeros below the diagonal)
   int64_t ldr;
-  double* partials;  // [2][nb][w]
+  double* partials;  // [2][w][nb]: slot-major so a warp reads one slot of all CTAs coalesced
   double* rowbuf;    // [2][w]
   WsHeader* hdr;
   int nb;
   int64_t rows_per;
+  int staged;        // 1: this CTA's rows live in shared memory for the whole kernel
 };
 
 // Bounded grid barrier.  Returns false (and records RRF_TIMEOUT) if the wait gave up.
@@ -61,7 +62,7 @@ __device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, unsigned& gen, int* s
           *s_fail = 1;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
     gen = target;
@@ -78,26 +79,26 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Partial sums of column j over this CTA's rows: slot j = sum_{i>j} x_i^2, slot k>j = sum_{i>=j} x_i P(i,k).
-__device__ void column_partials(const PanelArgs& a, int j, int64_t i0, int64_t i1, double* xs,
-                                double* out) {
+// Partial sums of column j over this CTA's rows (local panel Pl, local row l = global row i0 + l):
+// slot j = sum_{i>j} x_i^2, slot k>j = sum_{i>=j} x_i P(i,k).  Written to out[k * nb].
+__device__ void column_partials(const PanelArgs& a, int j, const double* Pl, int64_t ldl, int64_t i0, int64_t nloc,
+                                double* xs, double* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int64_t i = i0 + tid; i < i1; i += NT) xs[i - i0] = (i >= j) ? a.P[i + (int64_t)j * a.ldp] : 0.0;
+  for (int64_t l = tid; l < nloc; l += NT) xs[l] = (i0 + l >= j) ? Pl[l + (int64_t)j * ldl] : 0.0;
   __syncthreads();
+  const int64_t lb = (j > i0) ? (j - i0) : 0;  // first local row with i >= j
   for (int k = j + warp; k < a.w; k += NT / 32) {
     double acc = 0.0;
     if (k == j) {
-      for (int64_t i = i0 + lane; i < i1; i += 32)
-        if (i > j) acc = fma(xs[i - i0], xs[i - i0], acc);
+      for (int64_t l = lb + lane; l < nloc; l += 32)
+        if (i0 + l > j) acc = fma(xs[l], xs[l], acc);
     } else {
-      const double* pk = a.P + (int64_t)k * a.ldp;
-      for (int64_t i = i0 + lane; i < i1; i += 32)
-        if (i >= j) acc = fma(xs[i - i0], pk[i], acc);
+      const double* pk = Pl + (int64_t)k * ldl;
+      for (int64_t l = lb + lane; l < nloc; l += 32) acc = fma(xs[l], pk[l], acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) out[k] = acc;
+    if (lane == 0) out[(int64_t)k * a.nb] = acc;
   }
-  // The owner of row j publishes P(j, j:w).
   __syncthreads();
 }
 
@@ -107,36 +108,44 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
   __shared__ double zk[kMaxW];
   __shared__ double s_scalars[4];  // tau, beta, scal
   __shared__ int s_fail;
-  double* xs = smem;                  // rows_per
-  double* vs = smem + a.rows_per;     // rows_per
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cta = blockIdx.x;
   const int64_t i0 = std::min<int64_t>((int64_t)cta * a.rows_per, a.r);
   const int64_t i1 = std::min<int64_t>(i0 + a.rows_per, a.r);
+  const int64_t nloc = i1 - i0;
   const int w = a.w;
+  double* xs = smem;                   // rows_per
+  double* vs = smem + a.rows_per;      // rows_per
+  double* Pl = a.P + i0;               // local panel: global rows, or staged copy
+  int64_t ldl = a.ldp;
+  if (a.staged) {
+    Pl = smem + 2 * a.rows_per;
+    ldl = a.rows_per;
+    for (int k = warp; k < w; k += NT / 32)
+      for (int64_t l = lane; l < nloc; l += 32) Pl[l + k * ldl] = a.P[(i0 + l) + (int64_t)k * a.ldp];
+    __syncthreads();
+  }
   unsigned gen = 0;
   if (tid == 0) gen = *(volatile unsigned*)&a.hdr->bar_gen;
 
   // Phase 0: partials of column 0.
-  {
-    double* out = a.partials + ((int64_t)0 * a.nb + cta) * w;
-    column_partials(a, 0, i0, i1, xs, out);
-    if (0 >= i0 && 0 < i1)
-      for (int k = tid; k < w; k += NT) a.rowbuf[k] = a.P[(int64_t)k * a.ldp];
-  }
+  column_partials(a, 0, Pl, ldl, i0, nloc, xs, a.partials + cta);
+  if (i0 == 0 && nloc > 0)
+    for (int k = tid; k < w; k += NT) a.rowbuf[k] = Pl[(int64_t)k * ldl];
   if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
 
   for (int j = 0; j < w; ++j) {
     const int par = j & 1;
-    // Reduce the partial sums (CTA order) and read the owner's row j.
-    const double* part = a.partials + (int64_t)par * a.nb * w;
-    const double* row = a.rowbuf + (int64_t)par * w;
-    for (int k = j + tid; k < w; k += NT) {
-      double s = 0.0;
-      for (int c = 0; c < a.nb; ++c) s += __ldcg(part + (int64_t)c * w + k);
-      red[k] = s;
-      zk[k] = __ldcg(row + k);  // P(j, k)
+    // Reduce the partial sums: warp per slot, lanes over CTAs (coalesced), fixed shuffle tree.
+    const double* part = a.partials + (int64_t)par * w * a.nb;
+    for (int k = j + warp; k < w; k += NT / 32) {
+      double sum = 0.0;
+      for (int c = lane; c < a.nb; c += 32) sum += __ldcg(part + (int64_t)k * a.nb + c);
+      sum = warp_sum(sum);
+      if (lane == 0) red[k] = sum;
     }
+    const double* row = a.rowbuf + (int64_t)par * w;
+    for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);  // P(j, k)
     __syncthreads();
     if (tid == 0) {
       const double sig2 = red[j], alpha = zk[j];
@@ -157,47 +166,50 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
     // z_k = v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta); stored pre-multiplied by tau.
     for (int k = j + 1 + tid; k < w; k += NT) zk[k] = tau * ((red[k] - beta * zk[k]) * scal);
     // v over local rows (v_j = 1); column j becomes [beta; v(1:)].
-    for (int64_t i = i0 + tid; i < i1; i += NT) {
+    for (int64_t l = tid; l < nloc; l += NT) {
+      const int64_t i = i0 + l;
       double v = 0.0;
       if (i == j) {
         v = 1.0;
-        a.P[i + (int64_t)j * a.ldp] = beta;
+        Pl[l + (int64_t)j * ldl] = beta;
       } else if (i > j) {
-        v = (tau != 0.0) ? a.P[i + (int64_t)j * a.ldp] * scal : 0.0;
-        a.P[i + (int64_t)j * a.ldp] = v;
+        v = (tau != 0.0) ? Pl[l + (int64_t)j * ldl] * scal : 0.0;
+        Pl[l + (int64_t)j * ldl] = v;
       }
-      vs[i - i0] = v;
+      vs[l] = v;
     }
     __syncthreads();
     // Trailing update of the panel: P(i, k) -= tau z_k v_i for i >= j, k > j.
     if (tau != 0.0) {
-      const int lane = tid & 31, warp = tid >> 5;
-      const int64_t ib = std::max<int64_t>(i0, j);
+      const int64_t lb = (j > i0) ? (j - i0) : 0;
       for (int k = j + 1 + warp; k < w; k += NT / 32) {
-        double* pk = a.P + (int64_t)k * a.ldp;
+        double* pk = Pl + (int64_t)k * ldl;
         const double zz = zk[k];
-        for (int64_t i = ib + lane; i < i1; i += 32) pk[i] = fma(-zz, vs[i - i0], pk[i]);
+        for (int64_t l = lb + lane; l < nloc; l += 32) pk[l] = fma(-zz, vs[l], pk[l]);
       }
     }
     __syncthreads();
     if (j + 1 < w) {
-      double* out = a.partials + ((int64_t)((j + 1) & 1) * a.nb + cta) * w;
-      column_partials(a, j + 1, i0, i1, xs, out);
+      column_partials(a, j + 1, Pl, ldl, i0, nloc, xs, a.partials + (int64_t)((j + 1) & 1) * w * a.nb + cta);
       if ((j + 1) >= i0 && (j + 1) < i1) {
         double* rb = a.rowbuf + (int64_t)((j + 1) & 1) * w;
-        for (int k = j + 1 + tid; k < w; k += NT) rb[k] = a.P[(j + 1) + (int64_t)k * a.ldp];
+        const int64_t lj = (j + 1) - i0;
+        for (int k = j + 1 + tid; k < w; k += NT) rb[k] = Pl[lj + (int64_t)k * ldl];
       }
       if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
     }
   }
-  // Explicit reflectors Y (unit diagonal, zeros above) and the optional clean copy of R.
-  for (int k = 0; k < w; ++k) {
-    const double* pk = a.P + (int64_t)k * a.ldp;
+  // Write back (staged), explicit reflectors Y (unit diagonal, zeros above), optional clean copy of R.
+  for (int k = warp; k < w; k += NT / 32) {
+    const double* pk = Pl + (int64_t)k * ldl;
     double* yk = a.Y + (int64_t)k * a.ldy;
-    for (int64_t i = i0 + tid; i < i1; i += NT) yk[i] = (i < k) ? 0.0 : (i == k ? 1.0 : pk[i]);
-    if (a.Rout != nullptr)
-      for (int64_t i = i0 + tid; i < std::min<int64_t>(i1, w); i += NT)
-        a.Rout[i + (int64_t)k * a.ldr] = (i <= k) ? pk[i] : 0.0;
+    for (int64_t l = lane; l < nloc; l += 32) {
+      const int64_t i = i0 + l;
+      const double v = pk[l];
+      if (a.staged) a.P[i + (int64_t)k * a.ldp] = v;
+      yk[i] = (i < k) ? 0.0 : (i == k ? 1.0 : v);
+      if (a.Rout != nullptr && i < w) a.Rout[i + (int64_t)k * a.ldr] = (i <= k) ? v : 0.0;
+    }
   }
 }
 
@@ -278,13 +290,17 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   a.hdr = hdr;
   a.nb = nb;
   a.rows_per = (r + nb - 1) / nb;
-  const size_t dyn = (size_t)2 * a.rows_per * sizeof(double);
+  constexpr size_t kSmemCap = 200 * 1024;
+  size_t dyn = (size_t)2 * a.rows_per * sizeof(double);
+  const size_t staged_bytes = dyn + (size_t)a.rows_per * w * sizeof(double);
+  a.staged = staged_bytes <= kSmemCap ? 1 : 0;
+  if (a.staged) dyn = staged_bytes;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     attr_set = true;
   }
-  if (dyn > 200 * 1024) return cudaErrorInvalidValue;
+  if (dyn > kSmemCap) return cudaErrorInvalidValue;
   void* args[] = {(void*)&a};
   count_launch();
   e = cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(nb), dim3(NT), args, dyn, stream);

@@ -17,12 +17,6 @@
 
 namespace rrf {
 
-size_t sketch_bf16_scratch_bytes(int64_t m, int64_t n, int64_t b);
-cudaError_t sketch_bf16(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, const double* G,
-                        int q, double* Y, double* Z, double* Qtmp, char* scratch, size_t scratch_bytes,
-                        double* panel_scratch, size_t panel_bytes, double* gemm_scratch,
-                        size_t gemm_bytes, WsHeader* hdr, cudaStream_t stream);
-
 namespace {
 
 struct RWs {
@@ -36,9 +30,14 @@ struct RWs {
   size_t panel_bytes = 0;
   double* gemm = nullptr;
   size_t gemm_bytes = 0;
-  char* bf16 = nullptr;
-  size_t bf16_bytes = 0;
+  // BF16 sketch: T22 in BF16 twice (as stored, and transposed), the b-column operand, FP32 partials.
+  __nv_bfloat16 *Tb = nullptr, *Tbt = nullptr, *Xh = nullptr;
+  int64_t ldtb = 0, ldtbt = 0, ldxh = 0;
+  float* part = nullptr;
+  size_t part_bytes = 0;
 };
+
+int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
 
 size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, Arena& ar, RWs& w) {
   const int64_t mx = std::max(m, n);
@@ -68,8 +67,14 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, Arena& ar, RWs& w) {
   w.gemm_bytes = (size_t)16 * mx * b * sizeof(double);
   w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
   if (bf16) {
-    w.bf16_bytes = sketch_bf16_scratch_bytes(m, n, b);
-    w.bf16 = ar.take<char>(w.bf16_bytes);
+    w.ldtb = pad64(m);
+    w.ldtbt = pad64(n);
+    w.ldxh = pad64(mx);
+    w.Tb = ar.take<__nv_bfloat16>(w.ldtb * n);
+    w.Tbt = ar.take<__nv_bfloat16>(w.ldtbt * m);
+    w.Xh = ar.take<__nv_bfloat16>(w.ldxh * b);
+    w.part_bytes = (size_t)16 * mx * b * sizeof(float);
+    w.part = ar.take<float>((size_t)16 * mx * b);
   }
   return ar.off;
 }
@@ -122,6 +127,34 @@ cudaError_t sketch_fp64(int64_t r, int64_t c, int64_t b, const double* T22, int6
     if (e != cudaSuccess) break;
     GemmDesc gy = gd(c, b, r, T22, ldt, 1, zin, r, 0, w.Y, c);
     e = gemm_f64(&gy, 1, w.gemm, w.gemm_bytes, s);
+  }
+  return e;
+}
+
+// Sketch with BF16 operands on the tensor cores (FP32 accumulation).  T22 is rounded to BF16 once per
+// step, in both orientations so every product reads K-contiguous rows; the b-column sample is
+// orthonormalized in FP64 before each application of T22 and T22^T (Sec. 2.5 (ii)), because BF16
+// keeps only 8 bits and, unorthonormalized, (T22^T T22)^q would lose everything below
+// eps_bf16^(1/(2q+1)) sigma_max.
+cudaError_t sketch_bf16(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, int q, const RWs& w,
+                        cudaStream_t s) {
+  cudaError_t e = to_bf16(r, c, T22, ldt, w.Tb, w.ldtb, s);                 // column j = T22(:, j)
+  if (e == cudaSuccess) e = to_bf16_t(r, c, T22, ldt, w.Tbt, w.ldtbt, s);   // column i = T22(i, :)
+  if (e == cudaSuccess) e = to_bf16(r, b, w.G, r, w.Xh, w.ldxh, s);
+  if (e == cudaSuccess)
+    e = gemm_bf16_tn(c, b, r, w.Tb, w.ldtb, w.Xh, w.ldxh, 1.0, w.Y, c, w.part, w.part_bytes, &w.hdr->status, s);
+  for (int j = 0; j < q && e == cudaSuccess; ++j) {
+    e = panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+    if (e == cudaSuccess) e = explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s);
+    if (e == cudaSuccess) e = to_bf16(c, b, w.Qt, c, w.Xh, w.ldxh, s);
+    if (e == cudaSuccess)
+      e = gemm_bf16_tn(r, b, c, w.Tbt, w.ldtbt, w.Xh, w.ldxh, 1.0, w.Z, r, w.part, w.part_bytes, &w.hdr->status, s);
+    if (e == cudaSuccess)
+      e = panel_qr(r, b, w.Z, r, w.tauu, w.Yu, r, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+    if (e == cudaSuccess) e = explicit_q(r, b, w.Yu, w.Tu, w.Rs, w.Qt, w, s);
+    if (e == cudaSuccess) e = to_bf16(r, b, w.Qt, r, w.Xh, w.ldxh, s);
+    if (e == cudaSuccess)
+      e = gemm_bf16_tn(c, b, r, w.Tb, w.ldtb, w.Xh, w.ldxh, 1.0, w.Y, c, w.part, w.part_bytes, &w.hdr->status, s);
   }
   return e;
 }
@@ -212,8 +245,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       // Sketch.
       RRF_CUDA_TRY(randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s));
       if (bf16) {
-        RRF_CUDA_TRY(sketch_bf16(r, c, b, T22, ldt, w.G, qi, w.Y, w.Z, w.Qt, w.bf16, w.bf16_bytes, w.panel,
-                                 w.panel_bytes, w.gemm, w.gemm_bytes, w.hdr, s));
+        RRF_CUDA_TRY(sketch_bf16(r, c, b, T22, ldt, qi, w, s));
       } else {
         RRF_CUDA_TRY(sketch_fp64(r, c, b, T22, ldt, qi, reorth, w, s));
       }

@@ -1,6 +1,7 @@
 // rrf_internal.cuh -- shared declarations of the CUDA path (device kernels live in their own .cu files).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -101,6 +102,20 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
 // One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream);
+
+// ---- BF16 tensor-core GEMM (gemm_bf16_tc.cu) ------------------------------------------------------
+// D (FP64, M x N, ldd) = alpha * A (M x K) B (N x K)^T, BF16 operands with K contiguous (ld multiple of 8,
+// 16-byte aligned), FP32 accumulation on tcgen05; N <= 256.  part: FP32 split-K scratch.
+int tc_plan_splits(int64_t M, int64_t N, int64_t K);
+size_t tc_part_bytes(int64_t M, int64_t N, int64_t K);
+cudaError_t gemm_bf16_tn(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                         const __nv_bfloat16* B, int64_t ldb, double alpha, double* D, int64_t ldd, float* part,
+                         size_t part_bytes, int* status, cudaStream_t s);
+// FP64 column-major rows x cols -> BF16 with the same layout (ldd) or transposed (D[j + i ldd] = S(i, j)).
+cudaError_t to_bf16(int64_t rows, int64_t cols, const double* S, int64_t lds, __nv_bfloat16* D, int64_t ldd,
+                    cudaStream_t s);
+cudaError_t to_bf16_t(int64_t rows, int64_t cols, const double* S, int64_t lds, __nv_bfloat16* D, int64_t ldd,
+                      cudaStream_t s);
 
 // ---- small kernels (aux.cu) ------------------------------------------------------------------------
 cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);

@@ -27,6 +27,7 @@ EXPORTED = [
     "rrf_powerurv_host", "rrf_randn", "rrf_gemm_workspace", "rrf_gemm", "rrf_panel_qr_workspace", "rrf_panel_qr",
     "rrf_jacobi_svd_workspace", "rrf_jacobi_svd", "rrf_workspace_status", "rrf_status_string",
     "rrf_last_arg_error", "rrf_version", "rrf_launch_count", "rrf_gemm_profile_begin", "rrf_gemm_profile_end",
+    "rrf_gemm_bf16_workspace", "rrf_gemm_bf16",
 ]
 
 
@@ -95,6 +96,11 @@ def lib():
             L.rrf_last_arg_error.restype = ctypes.c_int
             L.rrf_version.restype = ctypes.c_char_p
             L.rrf_launch_count.restype = ctypes.c_int64
+            L.rrf_gemm_bf16_workspace.argtypes = [_i64, _i64, _i64]
+            L.rrf_gemm_bf16_workspace.restype = _sz
+            L.rrf_gemm_bf16.argtypes = [_i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz,
+                                        _vp]
+            L.rrf_gemm_bf16.restype = ctypes.c_int
             L.rrf_gemm_profile_begin.argtypes = [ctypes.c_int]
             L.rrf_gemm_profile_begin.restype = ctypes.c_int
             L.rrf_gemm_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -259,6 +265,24 @@ def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, 
                     _stream(stream))
     _check(st, "rrf_gemm")
     return C
+
+
+def gemm_bf16(A, B, alpha: float = 1.0, stream=None):
+    """D = alpha A B^T (FP64, column-major) from BF16 tensors A (m x k) and B (n x k) with contiguous rows
+    (row stride a multiple of 8 elements), FP32 accumulation on the tensor cores."""
+    torch = _torch()
+    L = lib()
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
+    assert A.stride(1) == 1 and B.stride(1) == 1
+    m, k = A.shape
+    n = B.shape[0]
+    D = fortran_empty(m, n, A.device)
+    ws = workspace(L.rrf_gemm_bf16_workspace(m, n, k), A.device)
+    st = L.rrf_gemm_bf16(m, n, k, alpha, _vp(A.data_ptr()), A.stride(0), _vp(B.data_ptr()), B.stride(0),
+                         _vp(D.data_ptr()), _ld(D), _vp(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(st, "rrf_gemm_bf16")
+    _check(L.rrf_workspace_status(_vp(ws.data_ptr()), _stream(stream)), "rrf_gemm_bf16 (device status)")
+    return D
 
 
 def panel_qr(P, want_tf: bool = True, stream=None):
