@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=2, help="randUTV steps the oracle runs per sample")
+    p.add_argument("--methods", default="randutv,powerurv", help="comma list (profiling runs may time one)")
     return p.parse_args()
 
 
@@ -175,14 +176,18 @@ def run_ours(args):
            "powerurv": rrf.workspace(rrf.powerurv_workspace_bytes(n, n, b), dev)}
     stream = torch.cuda.current_stream()
 
+    methods = [x for x in args.methods.split(",") if x]
+
     def step():
-        rrf.randutv(A, b, q, seed=17, out=outs["randutv"], ws=wss["randutv"], check_status=False)
-        rrf.powerurv(A, b, q, seed=17, out=outs["powerurv"], ws=wss["powerurv"], check_status=False)
+        if "randutv" in methods:
+            rrf.randutv(A, b, q, seed=17, out=outs["randutv"], ws=wss["randutv"], check_status=False)
+        if "powerurv" in methods:
+            rrf.powerurv(A, b, q, seed=17, out=outs["powerurv"], ws=wss["powerurv"], check_status=False)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    for name in ("randutv", "powerurv"):
+    for name in methods:
         st = rrf.lib().rrf_workspace_status(rrf._vp(wss[name].data_ptr()), rrf._stream(None))
         if st != 0:
             raise RuntimeError(f"{name}: device status {st}")
@@ -214,12 +219,13 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    flops = step_flops(n, b, q)
-    value = world * 2.0 / (ms / 1e3)
+    flops = (testmats.flops_randutv(n, n, b, q) if "randutv" in methods else 0.0) + \
+        (testmats.flops_powerurv(n, n, q) if "powerurv" in methods else 0.0)
+    value = world * len(methods) / (ms / 1e3)
 
     # Per-method device times (one more run each, outside the timed region).
     per = {}
-    for name in ("randutv", "powerurv"):
+    for name in methods:
         f = testmats.flops_randutv(n, n, b, q) if name == "randutv" else testmats.flops_powerurv(n, n, q)
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
@@ -277,7 +283,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 5), "unit": "factorizations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": ["randutv", "powerurv"],
+        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": methods,
                    "seeds": {"Q1": 11, "Q2": 12, "G": 17}, "l2": "inputs larger than L2 (A is 512 MB)",
                    "parallelism": f"replicas x{world}"},
         "tflops": round(world * flops / (ms / 1e3) / 1e12, 4),

@@ -118,6 +118,28 @@ RRF_API rrf_status rrf_powerurv_host(int64_t m, int64_t n, const double* A, int6
                              uint64_t seed, const rrf_opts* opts, void* stream);
 
 /* ------------------------------------------------------------------------------------------------
+ * Batched FP32 powerURV (Algorithm 1) for many matrices of uneven shape (m_i >= n_i, m_i <= 2^20).
+ * rrf_batch_plan_create fixes count, shapes (HOST arrays m, n), panel width b (1..64) and q; the
+ * workspace size follows from the plan.  rrf_powerurv_batched_f32 takes HOST arrays of DEVICE pointers
+ * (A_i read-only; U_i m x m, T_i m x n with R, V_i n x n written) and leading dimensions.  Its first call
+ * (and any call whose pointers, workspace, seed or stream differ from the previous one) uploads the
+ * descriptor table, autotunes the GEMM tile shape on the batch's own problems (first time only),
+ * captures the whole batched method as a CUDA graph and launches it; other calls replay the graph.
+ * Matrix i draws its Gaussian with key seed + i (step 0, tag 2): what rrf_powerurv draws for it with
+ * that seed.  Same Householder convention as the FP64 path, FP32 arithmetic throughout.
+ * rrf_batch_plan_tiles(plan, 0 | 1): index of the tile shape chosen for large | skinny GEMM phases. */
+typedef struct rrf_batch_plan rrf_batch_plan;
+RRF_API rrf_status rrf_batch_plan_create(rrf_batch_plan** plan, int count, const int64_t* m, const int64_t* n,
+                                         int64_t b, int q);
+RRF_API size_t rrf_batch_plan_workspace(const rrf_batch_plan* plan);
+RRF_API int rrf_batch_plan_tiles(const rrf_batch_plan* plan, int which);
+RRF_API rrf_status rrf_batch_plan_destroy(rrf_batch_plan* plan);
+RRF_API rrf_status rrf_powerurv_batched_f32(rrf_batch_plan* plan, const float* const* A, const int64_t* lda,
+                                            float* const* U, const int64_t* ldu, float* const* T,
+                                            const int64_t* ldt, float* const* V, const int64_t* ldv,
+                                            uint64_t seed, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
  * Building blocks, exported for kernel-level testing.  All pointers are device pointers; all calls
  * enqueue on `stream`.
  * ---------------------------------------------------------------------------------------------- */

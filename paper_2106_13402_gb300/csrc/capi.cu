@@ -13,6 +13,7 @@ thread_local int g_arg_error = 0;
 std::atomic<int64_t> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_arg_error(int pos) { g_arg_error = pos; }
 void clear_arg_error() { g_arg_error = 0; }
 

@@ -133,7 +133,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
         }
       }
       cluster.sync();
-      if (real) {
+      // (3) one lane per pair derives the rotation (FP64 division and square roots are scarce on this
+      // GPU, so the other lanes of the pair only receive cs, sn by shuffle), then all lanes rotate.
+      double cs = 1.0, sn = 0.0;
+      int rot = 0;
+      if (real && sub == 0) {
         double A = 0.0, B = 0.0, G = 0.0;
 #pragma unroll
         for (int rr = 0; rr < CL; ++rr) {
@@ -145,22 +149,31 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
         if (G != 0.0 && fabs(G) > tol * sqrt(A * B)) {
           const double zeta = (B - A) / (2.0 * G);
           const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tt * tt);
-          const double sn = cs * tt;
-          double* mp = Ml + p * ldl;
-          double* mq = Ml + q * ldl;
-          double* vp = Vl + p * ldl;
-          double* vq = Vl + q * ldl;
-          for (int i = sub; i < nloc; i += tpp) {
-            const double x = mp[i], y = mq[i];
-            mp[i] = cs * x - sn * y;
-            mq[i] = sn * x + cs * y;
-            const double u = vp[i], v = vq[i];
-            vp[i] = cs * u - sn * v;
-            vq[i] = sn * u + cs * v;
-          }
-          if (sub == 0) atomicAdd(&s_rot, 1);
+          cs = 1.0 / sqrt(1.0 + tt * tt);
+          sn = cs * tt;
+          rot = 1;
         }
+      }
+      if (tpp > 1) {
+        const int leader = (threadIdx.x & 31) & ~(tpp - 1);
+        cs = __shfl_sync(0xffffffffu, cs, leader);
+        sn = __shfl_sync(0xffffffffu, sn, leader);
+        rot = __shfl_sync(0xffffffffu, rot, leader);
+      }
+      if (real && rot) {
+        double* mp = Ml + p * ldl;
+        double* mq = Ml + q * ldl;
+        double* vp = Vl + p * ldl;
+        double* vq = Vl + q * ldl;
+        for (int i = sub; i < nloc; i += tpp) {
+          const double x = mp[i], y = mq[i];
+          mp[i] = cs * x - sn * y;
+          mq[i] = sn * x + cs * y;
+          const double u = vp[i], v = vq[i];
+          vp[i] = cs * u - sn * v;
+          vq[i] = sn * u + cs * v;
+        }
+        if (sub == 0) atomicAdd(&s_rot, 1);
       }
       par ^= 1;
       __syncthreads();
@@ -172,6 +185,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
     __syncthreads();
   }
   if (!converged && rank == 0 && tid == 0) set_status(&a.hdr->status, RRF_NOT_CONVERGED);
+  if (rank == 0 && tid == 0) a.hdr->flags[1] = sweep;  // diagnostics: sweeps of the last SVD
 
   // Column norms and the position of each v_k's largest-magnitude entry.
   for (int k = tid; k < c; k += NT) {

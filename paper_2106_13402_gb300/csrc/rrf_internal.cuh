@@ -61,6 +61,8 @@ const DevInfo& dev_info();
 
 // ---- launch accounting (every kernel launch of the library calls this once) -------------------------
 void count_launch();
+// adjust the counter by n (negative for captured-but-not-launched kernels, positive per graph replay)
+void add_launches(int64_t n);
 
 // ---- thread-local argument-error slot ------------------------------------------------------------
 void set_arg_error(int pos);

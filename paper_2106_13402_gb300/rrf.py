@@ -27,7 +27,8 @@ EXPORTED = [
     "rrf_powerurv_host", "rrf_randn", "rrf_gemm_workspace", "rrf_gemm", "rrf_panel_qr_workspace", "rrf_panel_qr",
     "rrf_jacobi_svd_workspace", "rrf_jacobi_svd", "rrf_workspace_status", "rrf_status_string",
     "rrf_last_arg_error", "rrf_version", "rrf_launch_count", "rrf_gemm_profile_begin", "rrf_gemm_profile_end",
-    "rrf_gemm_bf16_workspace", "rrf_gemm_bf16",
+    "rrf_gemm_bf16_workspace", "rrf_gemm_bf16", "rrf_batch_plan_create", "rrf_batch_plan_workspace",
+    "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32",
 ]
 
 
@@ -101,6 +102,20 @@ def lib():
             L.rrf_gemm_bf16.argtypes = [_i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz,
                                         _vp]
             L.rrf_gemm_bf16.restype = ctypes.c_int
+            L.rrf_batch_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
+                                                ctypes.POINTER(_i64), _i64, ctypes.c_int]
+            L.rrf_batch_plan_create.restype = ctypes.c_int
+            L.rrf_batch_plan_workspace.argtypes = [_vp]
+            L.rrf_batch_plan_workspace.restype = _sz
+            L.rrf_batch_plan_tiles.argtypes = [_vp, ctypes.c_int]
+            L.rrf_batch_plan_tiles.restype = ctypes.c_int
+            L.rrf_batch_plan_destroy.argtypes = [_vp]
+            L.rrf_batch_plan_destroy.restype = ctypes.c_int
+            pp = ctypes.POINTER(_vp)
+            L.rrf_powerurv_batched_f32.argtypes = [_vp, pp, ctypes.POINTER(_i64), pp, ctypes.POINTER(_i64), pp,
+                                                   ctypes.POINTER(_i64), pp, ctypes.POINTER(_i64), ctypes.c_uint64,
+                                                   _vp, _sz, _vp]
+            L.rrf_powerurv_batched_f32.restype = ctypes.c_int
             L.rrf_gemm_profile_begin.argtypes = [ctypes.c_int]
             L.rrf_gemm_profile_begin.restype = ctypes.c_int
             L.rrf_gemm_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -339,6 +354,62 @@ def gemm_profile_end():
     if lib().rrf_gemm_profile_end(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)) != 0:
         raise RuntimeError("rrf_gemm_profile_end failed")
     return ms.value, fl.value, n.value
+
+
+class BatchPlan:
+    """Batched FP32 powerURV over matrices of uneven shape (rrf_batch_plan_* / rrf_powerurv_batched_f32).
+    The first run autotunes, captures a CUDA graph and launches it; later runs with the same buffers replay
+    the graph."""
+
+    def __init__(self, shapes, b: int = 64, q: int = 1):
+        L = lib()
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        cnt = len(self.shapes)
+        ms = (_i64 * cnt)(*[m for m, _ in self.shapes])
+        ns = (_i64 * cnt)(*[n for _, n in self.shapes])
+        h = _vp()
+        _check(L.rrf_batch_plan_create(ctypes.byref(h), cnt, ms, ns, b, q), "rrf_batch_plan_create")
+        self._h = h
+        self.b, self.q = b, q
+
+    def workspace_bytes(self) -> int:
+        return int(lib().rrf_batch_plan_workspace(self._h))
+
+    def tiles(self):
+        L = lib()
+        return L.rrf_batch_plan_tiles(self._h, 0), L.rrf_batch_plan_tiles(self._h, 1)
+
+    def allocate(self, device="cuda"):
+        torch = _torch()
+        U = [fortran_empty(m, m, device, torch.float32) for m, n in self.shapes]
+        T = [fortran_empty(m, n, device, torch.float32) for m, n in self.shapes]
+        V = [fortran_empty(n, n, device, torch.float32) for m, n in self.shapes]
+        return U, T, V
+
+    def run(self, As, out, seed: int, ws, stream=None):
+        L = lib()
+        U, T, V = out
+        cnt = len(self.shapes)
+
+        def ptrs(xs):
+            return (_vp * cnt)(*[x.data_ptr() for x in xs])
+
+        def lds(xs):
+            return (_i64 * cnt)(*[_ld(x) for x in xs])
+
+        self._keep = [ptrs(As), lds(As), ptrs(U), lds(U), ptrs(T), lds(T), ptrs(V), lds(V)]
+        k = self._keep
+        st = L.rrf_powerurv_batched_f32(self._h, k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], seed,
+                                        _vp(ws.data_ptr()), ws.numel(), _stream(stream))
+        _check(st, "rrf_powerurv_batched_f32")
+        return U, T, V
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and _lib is not None:
+                _lib.rrf_batch_plan_destroy(self._h)
+        except Exception:
+            pass
 
 
 def version() -> str:
