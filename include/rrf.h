@@ -58,15 +58,32 @@ typedef enum {
 /* Precision of the sketch products Y = T22^T G and the power iterations (Algorithm 3). */
 enum { RRF_SKETCH_FP64 = 0, RRF_SKETCH_BF16 = 1 };
 
-/* Options; a NULL opts pointer means all defaults (FP64 sketch, no re-orthonormalization). */
+/* How the power-iteration count q of each randUTV step is chosen. */
+enum { RRF_Q_FIXED = 0, RRF_Q_LEARNED = 1 };
+
+/* How the FP64 products run.  RRF_GEMM_AUTO (default) and RRF_GEMM_NATIVE: the DFMA kernel.
+ * RRF_GEMM_EMULATED: products whose short side is >= 64, long side >= 128 and inner size >= 32 use the FP64
+ * emulation on the BF16 tensor cores (rrf_gemm_emulated), the rest the DFMA kernel. */
+enum { RRF_GEMM_AUTO = 0, RRF_GEMM_NATIVE = 1, RRF_GEMM_EMULATED = 2 };
+
+/* Options; a NULL opts pointer means all defaults (FP64 sketch, no re-orthonormalization, fixed q). */
 typedef struct rrf_opts {
   int sketch_prec;   /* RRF_SKETCH_FP64 (default) or RRF_SKETCH_BF16: the sketch GEMMs take BF16 operands
                         with FP32 accumulation on the tensor cores; everything else stays FP64.       */
   int reorth;        /* 1: orthonormalize the sample between applications of T22 and T22^T (Sec. 2.5
                         (ii)); forced on for the BF16 sketch.  0 follows Algorithm 3 literally.       */
   const int* q_per_block; /* optional HOST array of length ceil(n/b): power-iteration count of each
-                        step, overriding q (e.g. a learned policy); NULL uses q everywhere.           */
-  int reserved[4];   /* must be zero */
+                        step, overriding q; NULL uses q everywhere.                                  */
+  int q_policy;      /* RRF_Q_FIXED (default) or RRF_Q_LEARNED: each step first forms the q = 0 sketch,
+                        computes 16 features from it (see rrf_mlp_forward), runs the MLP whose FP16
+                        parameters mlp_params points to (DEVICE) and uses its argmax as that step's q;
+                        with mlp_params == NULL the fallback is the q argument.  The learned policy
+                        synchronizes the stream once per step (the host launches the chosen count). */
+  const void* mlp_params;
+  int* q_used_out;   /* optional HOST array [steps]: the q each step used                              */
+  float* features_out; /* optional HOST array [steps x 16]: the features of each step (learned policy) */
+  int gemm_mode;     /* RRF_GEMM_AUTO (default), RRF_GEMM_NATIVE or RRF_GEMM_EMULATED */
+  int reserved[3];   /* must be zero */
 } rrf_opts;
 
 /* ------------------------------------------------------------------------------------------------
@@ -156,6 +173,21 @@ RRF_API rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                     int64_t ldc, void* workspace, size_t ws_bytes, void* stream);
 
+/* FP64 GEMM emulated on the BF16 tensor cores (error-free splitting, Ozaki et al. 2012): same arguments and
+ * result convention as rrf_gemm.  Each row of op(A) and column of op(B) is scaled by a power of two and split
+ * into 7 signed 8-bit digits (exact in BF16; remainder below 2^-56 of the row / column maximum); the 28
+ * digit products of each 32-wide K chunk accumulate exactly in FP32 on tcgen05 and are folded into a
+ * double-float and then an FP64 accumulator.  The error is measured relative to the row and column maxima,
+ * not to (|op(A)||op(B)|)_ij: |error_ij| <~ 2K 2^-53 (|op(A)||op(B)|)_ij + 2^-46 K max_k|a_ik| max_k|b_kj|
+ * (worst case; random signs give about 2^-47.5 sqrt(K) max|a_i.| max|b_.j|), so entries far below their
+ * row / column scale lose relative accuracy that the native FP64 GEMM keeps.
+ * Needs max(m, n) >= 128, min(m, n) >= 64,
+ * k >= 32, and rrf_gemm_emulated_workspace(m, n, k) bytes of workspace. */
+RRF_API size_t rrf_gemm_emulated_workspace(int64_t m, int64_t n, int64_t k);
+RRF_API rrf_status rrf_gemm_emulated(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                                     double* C, int64_t ldc, void* workspace, size_t ws_bytes, void* stream);
+
 /* BF16 x BF16 GEMM with FP32 accumulation on the tensor cores (the products of the BF16 sketch,
  * Sec. 2.5: the range finder only needs a subspace): D = alpha A B^T, where A (m x k) and B (n x k) are
  * stored as rows of k contiguous BF16 values (raw 16-bit patterns), leading dimensions lda, ldb in
@@ -201,6 +233,24 @@ RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, doubl
  * stream capture.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating library routine. */
 RRF_API rrf_status rrf_panel_qr_noalloc(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
                                         int64_t ldy, int* status, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * The learned power-iteration policy (not in the paper: chooses q per randUTV step).  An MLP
+ * 16 -> 64 (ReLU) -> 64 (ReLU) -> 4 logits over q = 0..3, FP16 parameters packed as
+ * [W1 (64 x 16 row-major), b1, W2 (64 x 64), b2, W3 (4 x 64), b3] (rrf_mlp_param_count() values),
+ * FP16 activations, FP32 accumulation.  All pointers are DEVICE pointers; X is N x 16 row-major FP32,
+ * logits N x 4, labels N ints in 0..3.
+ * rrf_mlp_grad: mean softmax-cross-entropy loss (optional *loss) and its gradient (FP32, packed like the
+ *   parameters) over the N samples; workspace rrf_mlp_train_workspace(N) bytes.
+ * rrf_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master copy and moments
+ *   m, v (all packed like the parameters), refreshing the FP16 parameters; step counts from 1. */
+RRF_API int rrf_mlp_param_count(void);
+RRF_API size_t rrf_mlp_train_workspace(int N);
+RRF_API rrf_status rrf_mlp_forward(const void* params, const float* X, int N, float* logits, void* stream);
+RRF_API rrf_status rrf_mlp_grad(const void* params, const float* X, const int* labels, int N, float* grad,
+                                float* loss, void* workspace, size_t ws_bytes, void* stream);
+RRF_API rrf_status rrf_mlp_adam(float* master, float* m, float* v, const float* grad, void* params, int step,
+                                float lr, void* stream);
 
 /* Reads the device status word of a workspace used by any call above (synchronizes `stream`).
  * Returns RRF_OK or the first device-side condition the last call recorded. */

@@ -176,3 +176,56 @@ def powerurv(A, q: int, seed: int):
     V = np.zeros((n, n), order="F")
     st = lib().orc_powerurv(m, n, _p(A), m, q, seed, _p(U), m, _p(R), m, _p(V), n)
     return U, R, V, int(st)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Policy MLP reference (FP64 numpy): 16 -> 64 (ReLU) -> 64 (ReLU) -> 4, softmax cross-entropy.
+# Packing: [W1 (64 x 16, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (4 x 64), b3 (4)].
+MLP_SIZES = ((64, 16), (64,), (64, 64), (64,), (4, 64), (4,))
+
+
+def mlp_unpack(p):
+    p = np.asarray(p, dtype=np.float64)
+    out, o = [], 0
+    for shp in MLP_SIZES:
+        k = int(np.prod(shp))
+        out.append(p[o:o + k].reshape(shp))
+        o += k
+    return out
+
+
+def mlp_forward(p, X):
+    """Logits and activations: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(p)
+    X = np.asarray(X, dtype=np.float64)
+    a1 = X @ W1.T + b1
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ W2.T + b2
+    h2 = np.maximum(a2, 0.0)
+    z = h2 @ W3.T + b3
+    return z, (X, a1, h1, a2, h2)
+
+
+def mlp_loss_grad(p, X, labels):
+    """Mean softmax cross-entropy and its gradient by the chain rule (backpropagation), packed like p."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(p)
+    z, (X, a1, h1, a2, h2) = mlp_forward(p, X)
+    labels = np.asarray(labels)
+    N = X.shape[0]
+    zmax = z.max(axis=1, keepdims=True)
+    e = np.exp(z - zmax)
+    P = e / e.sum(axis=1, keepdims=True)
+    loss = float(np.mean(-np.log(P[np.arange(N), labels])))
+    dz = P.copy()
+    dz[np.arange(N), labels] -= 1.0
+    dz /= N
+    gW3 = dz.T @ h2
+    gb3 = dz.sum(axis=0)
+    dh2 = (dz @ W3) * (a2 > 0)
+    gW2 = dh2.T @ h1
+    gb2 = dh2.sum(axis=0)
+    dh1 = (dh2 @ W2) * (a1 > 0)
+    gW1 = dh1.T @ X
+    gb1 = dh1.sum(axis=0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    return loss, g

@@ -1,0 +1,560 @@
+// gemm_ozaki.cu -- FP64 GEMM emulated on the BF16 tensor cores (error-free splitting, Ozaki, Ogita, Oishi &
+// Rump, "Error-free transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 2012), for the compact-WY updates and sketch
+// products of Algorithms 1 and 3 on a GPU whose FP64 units are ~1/1600 of its BF16 tensor throughput.
+//
+// Splitting: row r of op(A) (length K) is scaled by 2^-e_r, where 2^e_r bounds its largest magnitude, and
+// written as S = 7 signed 8-bit digits per entry:  a = 2^e_r sum_s d_s 2^-8(s+1),  |d_0| <= 256,
+// |d_s| <= 128 -- every digit an exact BF16 value and every step exact in FP64; the dropped remainder is
+// below 2^-56 of the row maximum.  Columns of op(B) likewise (exponents f_c).
+// Products: sum_k d^A_i d^B_j over a 32-wide K chunk is an integer below 32 * 2^16 = 2^21, so the
+// tcgen05 MMA's FP32 accumulation is exact, and the up to 7 pairs (i, j) of one diagonal i + j = d fit
+// below 2^24 in one TMEM accumulator per diagonal.  After each chunk the 7 diagonal sums are folded into a
+// double-float (hi, lo) FP32 accumulator per output (error-free two-sum for the three leading diagonals,
+// a Horner sum of the rest, whose weight is below 2^-24 of the total, into lo), and every 16 chunks the
+// pair moves into an FP64 accumulator.  C = alpha 2^(e_r + f_c - 16) acc + beta C in FP64 at the end.
+//
+// Kernel roles (320 threads): warp 0 lane 0 loads 7 + 7 slice tiles per 32-wide K chunk with TMA (64-byte
+// swizzle, 2-stage ring); warp 1 lane 0 issues 56 MMAs (28 pairs x two K = 16 halves) per chunk into 7
+// TMEM accumulators of 64 columns; warps 2..9 read the accumulators (tcgen05.ld) and fold them.  All
+// mbarrier waits are bounded (RRF_TIMEOUT, drain, free TMEM, exit).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "rrf_internal.cuh"
+
+namespace rrf {
+namespace {
+
+constexpr int kS = 7;            // digits per value
+constexpr int BM = 128, BN = 64;
+constexpr int KC = 32;           // K per chunk / stage (64 bytes of BF16: 64-byte swizzle)
+constexpr int kStages = 2;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr long long kWaitCycles = 4000000000LL;
+constexpr uint32_t kTileA = BM * KC * 2;   // 8 KB per slice
+constexpr uint32_t kTileB = BN * KC * 2;   // 4 KB per slice
+constexpr uint32_t kStageBytes = kS * (kTileA + kTileB);
+
+struct OzParams {
+  int64_t M, N, Kp;     // Kp: padded K (multiple of KC)
+  int64_t kchunk;       // K per split (multiple of KC)
+  const int* ea;        // M row exponents
+  const int* eb;        // N column exponents
+  double alpha, beta;
+  double* C;            // splits == 1: C (ldc); else partials [split][N][M]
+  int64_t ldc;
+  int splits;
+  int ct;               // write C^T: element (row, col) at C[col + row ldc]
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+// K-major, 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
+  const uint64_t addr = (smem_u32(p) >> 4) & 0x3FFF;
+  return addr | (uint64_t(512 >> 4) << 32) | (uint64_t(1) << 46) | (uint64_t(4) << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      const __grid_constant__ OzParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t acc_full;
+  __shared__ __align__(8) uint64_t acc_empty;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int split = blockIdx.z;
+  const int64_t k0 = (int64_t)split * p.kchunk;
+  const int64_t k1 = min(p.Kp, k0 + p.kchunk);
+  const int nch = k1 > k0 ? (int)((k1 - k0) / KC) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, kEpiWarps);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nch; ++i) {
+        const int s = i % kStages;
+        if (i >= kStages && !mbar_wait(&empty_bar[s], ((i / kStages) - 1) & 1)) {
+          set_status(p.status, RRF_TIMEOUT);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int*)&abort_flag) break;
+        unsigned char* st = smem + s * kStageBytes;
+        mbar_expect_tx(&full_bar[s], kStageBytes);
+        const int kx = (int)(k0 + (int64_t)i * KC);
+        for (int sl = 0; sl < kS; ++sl) {
+          tma_load_2d(st + sl * kTileA, &map_a, &full_bar[s], kx, (int)(sl * p.M + m0));
+          tma_load_2d(st + kS * kTileA + sl * kTileB, &map_b, &full_bar[s], kx, (int)(sl * p.N + n0));
+        }
+        ++issued;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      for (int i = 0; i < nch; ++i) {
+        const int s = i % kStages;
+        if (!mbar_wait(&full_bar[s], (i / kStages) & 1) || (i > 0 && !mbar_wait(&acc_empty, (i - 1) & 1))) {
+          set_status(p.status, RRF_TIMEOUT);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = smem + s * kStageBytes;
+        for (int d = 0; d < kS; ++d) {
+          for (int a = 0; a <= d; ++a) {
+            const uint64_t da = smem_desc_sw64(st + a * kTileA);
+            const uint64_t db = smem_desc_sw64(st + kS * kTileA + (d - a) * kTileB);
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk)
+              mma_bf16(tmem + (uint32_t)(d * BN), da + 2 * kk, db + 2 * kk, idesc, (a > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+        mma_commit(&acc_full);
+      }
+    }
+  } else {
+    // Epilogue warps: ew 0..7; lanes 32 (ew % 4) .. of TMEM = tile rows, column half (ew / 4).
+    const int ew = warp - 2;
+    const int quad = warp & 3;        // TMEM lane quadrant this warp may access
+    const int col0 = (ew / 4) * 32;   // 32 of the 64 columns
+    float hi[32], lo[32];
+    double acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { hi[c] = 0.f; lo[c] = 0.f; acc[c] = 0.0; }
+    bool ok = true;
+    for (int i = 0; i < nch && ok; ++i) {
+      if (!mbar_wait(&acc_full, i & 1)) {
+        set_status(p.status, RRF_TIMEOUT);
+        atomicExch(&abort_flag, 1);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int cc = 0; cc < 32; cc += 8) {
+        uint32_t v[kS][8];
+#pragma unroll
+        for (int d = 0; d < kS; ++d)
+          tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(d * BN + col0 + cc), v[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          // Diagonals 0..2 enter the double-float (hi, lo) through an error-free two-sum; diagonals 3..6
+          // (weight <= 2^-24 of the total) are folded by Horner and added to lo.
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float x = __uint_as_float(v[d][c]) * (d == 0 ? 1.f : (d == 1 ? 0.00390625f : 1.52587890625e-05f));
+            const float sm = hi[cc + c] + x;
+            const float bb = sm - hi[cc + c];
+            const float err = (hi[cc + c] - (sm - bb)) + (x - bb);
+            hi[cc + c] = sm;
+            lo[cc + c] += err;
+          }
+          float tail = 0.f;
+#pragma unroll
+          for (int d = kS - 1; d >= 3; --d) tail = fmaf(tail, 0.00390625f, __uint_as_float(v[d][c]));
+          lo[cc + c] = fmaf(tail, 5.9604644775390625e-08f, lo[cc + c]);  // tail * 2^-24
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty);
+      // every 16 chunks (and at the end) move the double-float into an FP64 accumulator
+      if ((i & 15) == 15 || i == nch - 1) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          acc[c] += (double)hi[c] + (double)lo[c];
+          hi[c] = 0.f;
+          lo[c] = 0.f;
+        }
+      }
+    }
+    if (ok && nch > 0 && *(volatile int*)&abort_flag == 0) {
+      const int64_t row = m0 + quad * 32 + lane;
+      if (row < p.M) {
+        const int er = p.ea[row];
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+          const int64_t col = n0 + col0 + c;
+          if (col >= p.N) break;
+          const double v = ldexp(acc[c], er + p.eb[col] - 16);
+          if (p.splits == 1) {
+            double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
+            double out = p.alpha * v;
+            if (p.beta != 0.0) out = fma(p.beta, *cp, out);
+            *cp = out;
+          } else {
+            p.C[((int64_t)split * p.N + col) * p.M + row] = v;
+          }
+        }
+      }
+    } else if (nch == 0) {
+      const int64_t row = m0 + quad * 32 + lane;
+      if (row < p.M)
+        for (int c = 0; c < 32; ++c) {
+          const int64_t col = n0 + col0 + c;
+          if (col >= p.N) break;
+          if (p.splits == 1) {
+            double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
+            *cp = (p.beta != 0.0) ? p.beta * *cp : 0.0;
+          } else {
+            p.C[((int64_t)split * p.N + col) * p.M + row] = 0.0;
+          }
+        }
+    }
+  }
+  __syncthreads();
+  if (abort_flag && warp == 0 && lane == 0)
+    for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+      mbar_wait(&full_bar[i % kStages], (i / kStages) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+// Row exponents: e_r with max_k |X(r, k)| < 2^e_r (0 for an all-zero row).  X(r, k) = X[r sr + k sk].
+__global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restrict__ X, int64_t sr, int64_t sk,
+                                 int* __restrict__ e) {
+  if (sr == 1) {  // rows contiguous in memory across threads
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+      double mx = 0.0;
+      for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(X[r + k * sk]));
+      int ex = 0;
+      if (mx > 0.0) frexp(mx, &ex);
+      e[r] = ex;
+    }
+  } else {  // each row contiguous: one warp per row
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = wid; r < rows; r += nw) {
+      double mx = 0.0;
+      for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[r * sr + k]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) {
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        e[r] = ex;
+      }
+    }
+  }
+}
+
+// Digits: D[s][r][k] (row stride Kp, slice stride rows * Kp), zero for k >= K.  32 x 32 tiles.
+__global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const double* __restrict__ X, int64_t sr,
+                                int64_t sk, const int* __restrict__ e, __nv_bfloat16* __restrict__ D) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, kb = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    // read with the contiguous index on tx
+    int64_t r, k;
+    if (sr == 1) { r = r0 + tx; k = kb + j; } else { r = r0 + j; k = kb + tx; }
+    const double v = (r < rows && k < K) ? X[r * sr + k * sk] : 0.0;
+    if (sr == 1) tile[tx][j] = v; else tile[j][tx] = v;  // tile[row][k]
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = r0 + j, k = kb + tx;
+    if (r >= rows || k >= Kp) continue;
+    double t = ldexp(tile[j][tx], -e[r]);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+      t *= 256.0;
+      const double dg = rint(t);
+      t -= dg;
+      D[((int64_t)s * rows + r) * Kp + k] = __double2bfloat16(dg);
+    }
+  }
+}
+
+__global__ void oz_reduce_kernel(int64_t M, int64_t N, int splits, const double* __restrict__ part, double alpha,
+                                 double beta, double* __restrict__ C, int64_t ldc, int ct) {
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += part[sp * total + idx];
+    double* cp = ct ? C + (idx / M) + (idx % M) * ldc : C + (idx % M) + (idx / M) * ldc;
+    double v = alpha * s;
+    if (beta != 0.0) v = fma(beta, *cp, v);
+    *cp = v;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn oz_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+bool oz_map(CUtensorMap* map, const void* base, int64_t rows_total, int64_t Kp, int box_rows) {
+  EncodeTiledFn fn = oz_encode_fn();
+  if (fn == nullptr || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((Kp * 2) & 15) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows_total};
+  cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t oz_smem() { return (size_t)kStages * kStageBytes + 1024; }
+
+int oz_splits(int64_t M, int64_t N, int64_t Kp) {
+  const int sms = dev_info().sms;
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t chunks = Kp / KC;
+  int s = 1;
+  while (tiles * s * 2 <= 2 * sms && chunks / (s * 2) >= 8 && s < 16) s *= 2;
+  return s;
+}
+
+}  // namespace
+
+bool ozaki_eligible(const GemmDesc& d, bool force) {
+  const int64_t lo = std::min(d.M, d.N), hi = std::max(d.M, d.N);
+  return hi >= 128 && lo >= 64 && d.K >= 32 && (force || 2.0 * d.M * d.N * d.K >= 2.0e8);
+}
+
+size_t ozaki_bound(int64_t m, int64_t n, int64_t b) {
+  const int64_t mx = std::max(m, n);
+  return std::max({ozaki_scratch_bytes(mx, std::max<int64_t>(b, 64), mx), ozaki_scratch_bytes(mx, mx, b),
+                   ozaki_scratch_bytes(m, n, n)}) + 4096;
+}
+
+cudaError_t gemm_run(const GemmEngine& eng, const GemmDesc* d, int count, cudaStream_t s) {
+  GemmDesc rest[4];
+  int nrest = 0;
+  for (int i = 0; i < count; ++i) {
+    if (d[i].M <= 0 || d[i].N <= 0) continue;
+    if (eng.emulate && eng.oz != nullptr && ozaki_eligible(d[i], eng.force)) {
+      GemmDesc e = d[i];
+      bool ct = false;
+      if (e.M < e.N) {  // C^T = op(B)^T op(A)^T: put the long side on M
+        std::swap(e.M, e.N);
+        std::swap(e.A, e.B);
+        std::swap(e.lda, e.ldb);
+        const int ta = e.ta;
+        e.ta = !e.tb;
+        e.tb = !ta;
+        ct = true;
+      }
+      if (ozaki_scratch_bytes(e.M, e.N, e.K) <= eng.oz_bytes) {
+        cudaError_t err = gemm_ozaki(e, ct, eng.oz, eng.oz_bytes, eng.status, s);
+        if (err != cudaSuccess) return err;
+        continue;
+      }
+    }
+    rest[nrest++] = d[i];
+  }
+  if (nrest == 0) return cudaSuccess;
+  return gemm_f64(rest, nrest, eng.scratch, eng.scratch_bytes, s);
+}
+
+size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K) {
+  const int64_t Kp = (K + KC - 1) / KC * KC;
+  size_t b = align_up((size_t)kS * M * Kp * 2, 256) + align_up((size_t)kS * N * Kp * 2, 256);
+  b += align_up(sizeof(int) * M, 256) + align_up(sizeof(int) * N, 256);
+  b += align_up((size_t)oz_splits(M, N, Kp) * M * N * sizeof(double), 256);
+  return b;
+}
+
+cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, size_t scratch_bytes, int* status,
+                       cudaStream_t s) {
+  if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+  const int64_t M = d.M, N = d.N, K = d.K;
+  const int64_t Kp = (K + KC - 1) / KC * KC;
+  if (ozaki_scratch_bytes(M, N, K) > scratch_bytes) return cudaErrorInvalidValue;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = scratch + off; off += align_up(bytes, 256); return p; };
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(take((size_t)kS * M * Kp * 2));
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(take((size_t)kS * N * Kp * 2));
+  int* ea = reinterpret_cast<int*>(take(sizeof(int) * M));
+  int* eb = reinterpret_cast<int*>(take(sizeof(int) * N));
+  const int splits = oz_splits(M, N, Kp);
+  double* part = reinterpret_cast<double*>(take((size_t)splits * M * N * sizeof(double)));
+  // op(A)(m, k) = A[m + k lda] or A[k + m lda]; op(B)^T(n, k) = op(B)(k, n) = B[k + n ldb] or B[n + k ldb]
+  const int64_t asr = d.ta ? d.lda : 1, ask = d.ta ? 1 : d.lda;
+  const int64_t bsr = d.tb ? 1 : d.ldb, bsk = d.tb ? d.ldb : 1;
+  const int sms = dev_info().sms;
+  oz_rowexp_kernel<<<sms * 8, 256, 0, s>>>(M, K, d.A, asr, ask, ea);
+  count_launch();
+  oz_rowexp_kernel<<<sms * 8, 256, 0, s>>>(N, K, d.B, bsr, bsk, eb);
+  count_launch();
+  oz_split_kernel<<<dim3((unsigned)((M + 31) / 32), (unsigned)(Kp / 32)), dim3(32, 8), 0, s>>>(M, K, Kp, d.A, asr, ask,
+                                                                                            ea, As);
+  count_launch();
+  oz_split_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)(Kp / 32)), dim3(32, 8), 0, s>>>(N, K, Kp, d.B, bsr, bsk,
+                                                                                            eb, Bs);
+  count_launch();
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, As, kS * M, Kp, BM) || !oz_map(&mb, Bs, kS * N, Kp, BN)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  OzParams p;
+  p.M = M; p.N = N; p.Kp = Kp;
+  p.kchunk = ((Kp / KC + splits - 1) / splits) * KC;
+  p.ea = ea; p.eb = eb;
+  p.alpha = d.alpha; p.beta = d.beta;
+  p.splits = splits;
+  p.C = splits == 1 ? d.C : part;
+  p.ldc = d.ldc;
+  p.ct = out_transposed ? 1 : 0;
+  p.status = status;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+  ozaki_gemm_kernel<<<grid, kThreads, oz_smem(), s>>>(ma, mb, p);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const int64_t blocks = std::min<int64_t>((M * N + 255) / 256, (int64_t)sms * 16);
+  oz_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(M, N, splits, part, d.alpha, d.beta, d.C, d.ldc, p.ct);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rrf
+
+using namespace rrf;
+
+extern "C" size_t rrf_gemm_emulated_workspace(int64_t m, int64_t n, int64_t k) {
+  if (m < 1 || n < 1 || k < 1) return kHeaderBytes;
+  return kHeaderBytes + ozaki_scratch_bytes(std::max(m, n), std::min(m, n), k) + 256;
+}
+
+extern "C" rrf_status rrf_gemm_emulated(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                                        double* C, int64_t ldc, void* workspace, size_t ws_bytes, void* stream) {
+  clear_arg_error();
+  const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') { set_arg_error(1); return RRF_INVALID_ARG; }
+  if (!tb && transb != 'N' && transb != 'n') { set_arg_error(2); return RRF_INVALID_ARG; }
+  if (std::max(m, n) < 128 || std::min(m, n) < 64) { set_arg_error(3); return RRF_UNSUPPORTED; }
+  if (k < 32) { set_arg_error(5); return RRF_UNSUPPORTED; }
+  if (A == nullptr || lda < std::max<int64_t>(1, ta ? k : m)) { set_arg_error(8); return RRF_INVALID_ARG; }
+  if (B == nullptr || ldb < std::max<int64_t>(1, tb ? n : k)) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (C == nullptr || ldc < std::max<int64_t>(1, m)) { set_arg_error(13); return RRF_INVALID_ARG; }
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) { set_arg_error(14); return RRF_INVALID_ARG; }
+  if (ws_bytes < rrf_gemm_emulated_workspace(m, n, k)) { set_arg_error(15); return RRF_WORKSPACE_TOO_SMALL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(workspace);
+  RRF_CUDA_TRY(cudaMemsetAsync(hdr, 0, kHeaderBytes, s));
+  GemmEngine eng;
+  eng.oz = reinterpret_cast<char*>(workspace) + kHeaderBytes;
+  eng.oz_bytes = ws_bytes - kHeaderBytes;
+  eng.status = &hdr->status;
+  eng.emulate = true;
+  eng.force = true;
+  GemmDesc g;
+  g.M = m; g.N = n; g.K = k;
+  g.A = A; g.lda = lda; g.ta = ta;
+  g.B = B; g.ldb = ldb; g.tb = tb;
+  g.C = C; g.ldc = ldc;
+  g.alpha = alpha; g.beta = beta;
+  RRF_CUDA_TRY(gemm_run(eng, &g, 1, s));
+  return RRF_OK;
+}

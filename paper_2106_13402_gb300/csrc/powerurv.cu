@@ -21,9 +21,10 @@ struct PWs {
   size_t panel_bytes = 0;
   double* gemm = nullptr;
   size_t gemm_bytes = 0;
+  GemmEngine eng;
 };
 
-size_t layout(int64_t m, int64_t n, int64_t b, Arena& ar, PWs& w) {
+size_t layout(int64_t m, int64_t n, int64_t b, int gemm_mode, Arena& ar, PWs& w) {
   const int64_t mx = std::max(m, n);
   const int64_t nblk = (n + b - 1) / b;
   w.hdr = reinterpret_cast<WsHeader*>(ar.take<char>(kHeaderBytes));
@@ -37,6 +38,15 @@ size_t layout(int64_t m, int64_t n, int64_t b, Arena& ar, PWs& w) {
   w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
   w.gemm_bytes = (size_t)16 * mx * b * sizeof(double);
   w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
+  w.eng.scratch = w.gemm;
+  w.eng.scratch_bytes = w.gemm_bytes;
+  w.eng.status = w.hdr ? &w.hdr->status : nullptr;
+  w.eng.emulate = gemm_mode == RRF_GEMM_EMULATED;
+  w.eng.force = gemm_mode == RRF_GEMM_EMULATED;
+  if (w.eng.emulate) {
+    w.eng.oz_bytes = ozaki_bound(m, n, b);
+    w.eng.oz = ar.take<char>(w.eng.oz_bytes);
+  }
   return ar.off;
 }
 
@@ -67,11 +77,11 @@ cudaError_t blocked_hqr(int64_t rows, int64_t cols, double* X, int64_t ldx, int6
     if (nc <= 0) continue;
     double* C = X + j0 + (j0 + wd) * ldx;
     GemmDesc g1 = gd(wd, nc, rr, Yj, rows, 1, C, ldx, 0, w.Wa, b);
-    if ((e = gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g1, 1, s)) != cudaSuccess) return e;
     GemmDesc g2 = gd(wd, nc, wd, Tj, b, 1, w.Wa, b, 0, w.Wb, b);
-    if ((e = gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g2, 1, s)) != cudaSuccess) return e;
     GemmDesc g3 = gd(rr, nc, wd, Yj, rows, 0, w.Wb, b, 0, C, ldx, -1.0, 1.0);
-    if ((e = gemm_f64(&g3, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g3, 1, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -92,11 +102,11 @@ cudaError_t form_q(int64_t rows, int64_t ncols, int64_t k, int64_t b, double* Q,
     const double* Tj = w.Tall + jb * b * b;
     double* C = Q + j0 + j0 * ldq;
     GemmDesc g1 = gd(wd, nc, rr, Yj, rows, 1, C, ldq, 0, w.Wa, b);
-    if ((e = gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g1, 1, s)) != cudaSuccess) return e;
     GemmDesc g2 = gd(wd, nc, wd, Tj, b, 0, w.Wa, b, 0, w.Wb, b);
-    if ((e = gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g2, 1, s)) != cudaSuccess) return e;
     GemmDesc g3 = gd(rr, nc, wd, Yj, rows, 0, w.Wb, b, 0, C, ldq, -1.0, 1.0);
-    if ((e = gemm_f64(&g3, 1, w.gemm, w.gemm_bytes, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(w.eng, &g3, 1, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -106,11 +116,11 @@ cudaError_t form_q(int64_t rows, int64_t ncols, int64_t k, int64_t b, double* Q,
 
 using namespace rrf;
 
-extern "C" size_t rrf_powerurv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts*) {
+extern "C" size_t rrf_powerurv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts) {
   if (m < 1 || n < 1 || b < 1) return 0;
   Arena ar;
   PWs w;
-  return layout(m, n, b, ar, w);
+  return layout(m, n, b, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
 }
 
 extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
@@ -131,7 +141,9 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   if (ldt < m) { set_arg_error(10); return RRF_INVALID_ARG; }
   if (V == nullptr) { set_arg_error(11); return RRF_INVALID_ARG; }
   if (ldv < n) { set_arg_error(12); return RRF_INVALID_ARG; }
-  if (opts != nullptr && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->q_per_block != nullptr)) {
+  if (opts != nullptr && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->q_per_block != nullptr ||
+                          opts->q_policy != RRF_Q_FIXED || opts->gemm_mode < RRF_GEMM_AUTO ||
+                          opts->gemm_mode > RRF_GEMM_EMULATED)) {
     set_arg_error(16);
     return RRF_UNSUPPORTED;
   }
@@ -148,7 +160,7 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   ar.base = reinterpret_cast<char*>(workspace);
   ar.cap = ws_bytes;
   PWs w;
-  layout(m, n, b, ar, w);
+  layout(m, n, b, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
   if (ar.overflow) return RRF_WORKSPACE_TOO_SMALL;
 
   RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
@@ -162,16 +174,16 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   }
   for (int it = 0; it < q; ++it) {
     GemmDesc g1 = gd(m, n, n, A, lda, 0, V, ldv, 0, w.W, m);           // Yh = A V
-    RRF_CUDA_TRY(gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s));
+    RRF_CUDA_TRY(gemm_run(w.eng, &g1, 1, s));
     RRF_CUDA_TRY(blocked_hqr(m, n, w.W, m, b, w, s));                  // Vh = HQR_thin(Yh) -> T
     RRF_CUDA_TRY(form_q(m, n, n, b, T, ldt, w, s));
     GemmDesc g2 = gd(n, n, m, A, lda, 1, T, ldt, 0, w.W, n);           // Y = A^T Vh
-    RRF_CUDA_TRY(gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s));
+    RRF_CUDA_TRY(gemm_run(w.eng, &g2, 1, s));
     RRF_CUDA_TRY(blocked_hqr(n, n, w.W, n, b, w, s));                  // V = HQR_thin(Y)
     RRF_CUDA_TRY(form_q(n, n, n, b, V, ldv, w, s));
   }
   GemmDesc g3 = gd(m, n, n, A, lda, 0, V, ldv, 0, T, ldt);             // Ah = A V
-  RRF_CUDA_TRY(gemm_f64(&g3, 1, w.gemm, w.gemm_bytes, s));
+  RRF_CUDA_TRY(gemm_run(w.eng, &g3, 1, s));
   RRF_CUDA_TRY(blocked_hqr(m, n, T, ldt, b, w, s));                    // [U, R] = HQR_full(Ah)
   RRF_CUDA_TRY(form_q(m, m, n, b, U, ldu, w, s));
   RRF_CUDA_TRY(zero_lower(m, n, T, ldt, s));

@@ -30,16 +30,21 @@ struct RWs {
   size_t panel_bytes = 0;
   double* gemm = nullptr;
   size_t gemm_bytes = 0;
+  GemmEngine eng;
   // BF16 sketch: T22 in BF16 twice (as stored, and transposed), the b-column operand, FP32 partials.
   __nv_bfloat16 *Tb = nullptr, *Tbt = nullptr, *Xh = nullptr;
   int64_t ldtb = 0, ldtbt = 0, ldxh = 0;
   float* part = nullptr;
   size_t part_bytes = 0;
+  // learned q policy: features of the current step, the chosen q, a scratch scalar
+  float* feat = nullptr;
+  int* qdev = nullptr;
+  double* fro2 = nullptr;
 };
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
 
-size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, Arena& ar, RWs& w) {
+size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& ar, RWs& w) {
   const int64_t mx = std::max(m, n);
   w.hdr = reinterpret_cast<WsHeader*>(ar.take<char>(kHeaderBytes));
   w.G = ar.take<double>(m * b);
@@ -62,10 +67,22 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, Arena& ar, RWs& w) {
   w.Us = ar.take<double>(b * b);
   w.Vs = ar.take<double>(b * b);
   w.sig = ar.take<double>(b);
+  w.feat = ar.take<float>(16);
+  w.qdev = ar.take<int>(4);
+  w.fro2 = ar.take<double>(4);
   w.panel_bytes = panel_scratch_bytes(mx, b);
   w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
   w.gemm_bytes = (size_t)16 * mx * b * sizeof(double);
   w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
+  w.eng.scratch = w.gemm;
+  w.eng.scratch_bytes = w.gemm_bytes;
+  w.eng.status = w.hdr ? &w.hdr->status : nullptr;
+  w.eng.emulate = gemm_mode == RRF_GEMM_EMULATED;
+  w.eng.force = gemm_mode == RRF_GEMM_EMULATED;
+  if (w.eng.emulate) {
+    w.eng.oz_bytes = ozaki_bound(m, n, b);
+    w.eng.oz = ar.take<char>(w.eng.oz_bytes);
+  }
   if (bf16) {
     w.ldtb = pad64(m);
     w.ldtbt = pad64(n);
@@ -94,67 +111,74 @@ GemmDesc gd(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, int t
 cudaError_t explicit_q(int64_t rows, int64_t k, const double* Yr, const double* Tr, double* Wkk, double* Q,
                        const RWs& w, cudaStream_t s) {
   GemmDesc g1 = gd(k, k, k, Tr, k, 0, Yr, rows, 1, Wkk, k);
-  cudaError_t e = gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s);
+  cudaError_t e = gemm_run(w.eng, &g1, 1, s);
   if (e != cudaSuccess) return e;
   e = fill_identity(rows, k, Q, rows, s);
   if (e != cudaSuccess) return e;
   GemmDesc g2 = gd(rows, k, k, Yr, rows, 0, Wkk, k, 0, Q, rows, -1.0, 1.0);
-  return gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s);
+  return gemm_run(w.eng, &g2, 1, s);
 }
 
-// Sketch Y = (T22^T T22)^q T22^T G in FP64; with reorth, the sample is orthonormalized before
-// every application of T22 and of T22^T (Sec. 2.5 (ii)).
-cudaError_t sketch_fp64(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, int q, bool reorth,
-                        const RWs& w, cudaStream_t s) {
-  GemmDesc g = gd(c, b, r, T22, ldt, 1, w.G, r, 0, w.Y, c);
-  cudaError_t e = gemm_f64(&g, 1, w.gemm, w.gemm_bytes, s);
-  for (int j = 0; j < q && e == cudaSuccess; ++j) {
-    const double* yin = w.Y;
-    if (reorth) {
-      e = panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
-      if (e == cudaSuccess) e = explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s);
-      yin = w.Qt;
-    }
-    if (e != cudaSuccess) break;
-    GemmDesc gz = gd(r, b, c, T22, ldt, 0, yin, c, 0, w.Z, r);
-    e = gemm_f64(&gz, 1, w.gemm, w.gemm_bytes, s);
-    const double* zin = w.Z;
-    if (reorth && e == cudaSuccess) {
-      e = panel_qr(r, b, w.Z, r, w.tauu, w.Yu, r, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
-      if (e == cudaSuccess) e = explicit_q(r, b, w.Yu, w.Tu, w.Rs, w.Qt, w, s);
-      zin = w.Qt;
-    }
-    if (e != cudaSuccess) break;
-    GemmDesc gy = gd(c, b, r, T22, ldt, 1, zin, r, 0, w.Y, c);
-    e = gemm_f64(&gy, 1, w.gemm, w.gemm_bytes, s);
+// Y0 = T22^T G into Y: FP64 DFMA GEMM, or BF16 tensor cores after rounding T22 (both orientations) and G.
+cudaError_t sketch_begin(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, bool bf16, const RWs& w,
+                         cudaStream_t s) {
+  if (!bf16) {
+    GemmDesc g = gd(c, b, r, T22, ldt, 1, w.G, r, 0, w.Y, c);
+    return gemm_run(w.eng, &g, 1, s);
   }
-  return e;
-}
-
-// Sketch with BF16 operands on the tensor cores (FP32 accumulation).  T22 is rounded to BF16 once per
-// step, in both orientations so every product reads K-contiguous rows; the b-column sample is
-// orthonormalized in FP64 before each application of T22 and T22^T (Sec. 2.5 (ii)), because BF16
-// keeps only 8 bits and, unorthonormalized, (T22^T T22)^q would lose everything below
-// eps_bf16^(1/(2q+1)) sigma_max.
-cudaError_t sketch_bf16(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, int q, const RWs& w,
-                        cudaStream_t s) {
   cudaError_t e = to_bf16(r, c, T22, ldt, w.Tb, w.ldtb, s);                 // column j = T22(:, j)
   if (e == cudaSuccess) e = to_bf16_t(r, c, T22, ldt, w.Tbt, w.ldtbt, s);   // column i = T22(i, :)
   if (e == cudaSuccess) e = to_bf16(r, b, w.G, r, w.Xh, w.ldxh, s);
   if (e == cudaSuccess)
     e = gemm_bf16_tn(c, b, r, w.Tb, w.ldtb, w.Xh, w.ldxh, 1.0, w.Y, c, w.part, w.part_bytes, &w.hdr->status, s);
+  return e;
+}
+
+// out = T22 * in (r x b) or T22^T * in (c x b), FP64 or BF16 (in is FP64; rounded for the BF16 form).
+cudaError_t apply_t22(bool transposed, int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, bool bf16,
+                      const double* in, double* out, const RWs& w, cudaStream_t s) {
+  const int64_t K = transposed ? r : c, M = transposed ? c : r;
+  if (!bf16) {
+    GemmDesc g = gd(M, b, K, T22, ldt, transposed ? 1 : 0, in, K, 0, out, M);
+    return gemm_run(w.eng, &g, 1, s);
+  }
+  cudaError_t e = to_bf16(K, b, in, K, w.Xh, w.ldxh, s);
+  if (e != cudaSuccess) return e;
+  return gemm_bf16_tn(M, b, K, transposed ? w.Tb : w.Tbt, transposed ? w.ldtb : w.ldtbt, w.Xh, w.ldxh, 1.0, out, M,
+                      w.part, w.part_bytes, &w.hdr->status, s);
+}
+
+// Orthonormal basis (explicit thin Q, rows x b) of X via the panel Householder QR; X is overwritten.
+cudaError_t orthonormalize(int64_t rows, int64_t b, double* X, double* Qout, const RWs& w, cudaStream_t s) {
+  cudaError_t e = panel_qr(rows, b, X, rows, w.tauu, w.Yu, rows, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+  if (e == cudaSuccess) e = explicit_q(rows, b, w.Yu, w.Tu, w.Rs, Qout, w, s);
+  return e;
+}
+
+// q further applications: Y <- T22^T (T22 Y).  With reorth (always for BF16) the sample is orthonormalized
+// before every application of T22 and of T22^T (Sec. 2.5 (ii)); `start` (optional) is an orthonormal
+// basis of the current Y that the caller already has.  BF16 keeps only 8 bits: unorthonormalized,
+// (T22^T T22)^q would lose everything below eps_bf16^(1/(2q+1)) sigma_max.
+cudaError_t sketch_continue(int64_t r, int64_t c, int64_t b, const double* T22, int64_t ldt, int q, bool bf16,
+                            bool reorth, const double* start, const RWs& w, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   for (int j = 0; j < q && e == cudaSuccess; ++j) {
-    e = panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
-    if (e == cudaSuccess) e = explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s);
-    if (e == cudaSuccess) e = to_bf16(c, b, w.Qt, c, w.Xh, w.ldxh, s);
-    if (e == cudaSuccess)
-      e = gemm_bf16_tn(r, b, c, w.Tbt, w.ldtbt, w.Xh, w.ldxh, 1.0, w.Z, r, w.part, w.part_bytes, &w.hdr->status, s);
-    if (e == cudaSuccess)
-      e = panel_qr(r, b, w.Z, r, w.tauu, w.Yu, r, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
-    if (e == cudaSuccess) e = explicit_q(r, b, w.Yu, w.Tu, w.Rs, w.Qt, w, s);
-    if (e == cudaSuccess) e = to_bf16(r, b, w.Qt, r, w.Xh, w.ldxh, s);
-    if (e == cudaSuccess)
-      e = gemm_bf16_tn(c, b, r, w.Tb, w.ldtb, w.Xh, w.ldxh, 1.0, w.Y, c, w.part, w.part_bytes, &w.hdr->status, s);
+    const double* yin = w.Y;
+    if (reorth) {
+      if (j == 0 && start != nullptr) {
+        yin = start;
+      } else {
+        e = orthonormalize(c, b, w.Y, w.Qt, w, s);
+        yin = w.Qt;
+      }
+    }
+    if (e == cudaSuccess) e = apply_t22(false, r, c, b, T22, ldt, bf16, yin, w.Z, w, s);
+    const double* zin = w.Z;
+    if (reorth && e == cudaSuccess) {
+      e = orthonormalize(r, b, w.Z, w.Qt, w, s);
+      zin = w.Qt;
+    }
+    if (e == cudaSuccess) e = apply_t22(true, r, c, b, T22, ldt, bf16, zin, w.Y, w, s);
   }
   return e;
 }
@@ -179,8 +203,11 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
     if (opts->sketch_prec != RRF_SKETCH_FP64 && opts->sketch_prec != RRF_SKETCH_BF16) {
       set_arg_error(16); return RRF_INVALID_ARG;
     }
-    for (int i = 0; i < 4; ++i)
+    if (opts->q_policy != RRF_Q_FIXED && opts->q_policy != RRF_Q_LEARNED) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->q_policy == RRF_Q_LEARNED && opts->q_per_block != nullptr) { set_arg_error(16); return RRF_INVALID_ARG; }
+    for (int i = 0; i < 3; ++i)
       if (opts->reserved[i] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->gemm_mode < RRF_GEMM_AUTO || opts->gemm_mode > RRF_GEMM_EMULATED) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->q_per_block != nullptr) {
       const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
       for (int64_t i = 0; i < steps; ++i)
@@ -200,7 +227,7 @@ extern "C" size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const r
   Arena ar;
   RWs w;
   const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;
-  return layout(m, n, b, bf16, ar, w);
+  return layout(m, n, b, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
 }
 
 extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
@@ -225,7 +252,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   ar.base = reinterpret_cast<char*>(workspace);
   ar.cap = ws_bytes;
   RWs w;
-  layout(m, n, b, bf16, ar, w);
+  layout(m, n, b, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
   if (ar.overflow) return RRF_WORKSPACE_TOO_SMALL;
 
   RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
@@ -236,19 +263,45 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   RRF_CUDA_TRY(fill_identity(n, n, V, ldv, s));
 
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
+  const bool learned = opts != nullptr && opts->q_policy == RRF_Q_LEARNED;
+  int q_prev = q;
   for (int64_t i = 1; i <= steps; ++i) {
     const int64_t o = b * (i - 1);
     const int64_t r = m - o, c = n - o;
     double* T22 = T + o + o * ldt;
     if (b * i < m && b * i < n) {
-      const int qi = (opts != nullptr && opts->q_per_block != nullptr) ? opts->q_per_block[i - 1] : q;
+      int qi = (opts != nullptr && opts->q_per_block != nullptr) ? opts->q_per_block[i - 1] : q;
       // Sketch.
       RRF_CUDA_TRY(randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s));
-      if (bf16) {
-        RRF_CUDA_TRY(sketch_bf16(r, c, b, T22, ldt, qi, w, s));
-      } else {
-        RRF_CUDA_TRY(sketch_fp64(r, c, b, T22, ldt, qi, reorth, w, s));
+      RRF_CUDA_TRY(sketch_begin(r, c, b, T22, ldt, bf16, w, s));
+      const double* start = nullptr;
+      if (learned) {
+        // Features from the q = 0 sketch (the R of its Householder QR), MLP -> q for this step.
+        RRF_CUDA_TRY(copy_matrix(c, b, w.Y, c, w.Qt, c, s));
+        RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s));
+        RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, w.Y, c, w.fro2, (int)i, (int)steps, n, q_prev, w.feat, s));
+        if (opts->mlp_params != nullptr) {
+          RRF_CUDA_TRY(policy_decide(opts->mlp_params, w.feat, w.qdev, s));
+          int qh = q;
+          RRF_CUDA_TRY(cudaMemcpyAsync(&qh, w.qdev, sizeof(int), cudaMemcpyDeviceToHost, s));
+          if (opts->features_out != nullptr)
+            RRF_CUDA_TRY(cudaMemcpyAsync(opts->features_out + 16 * (i - 1), w.feat, 16 * sizeof(float),
+                                         cudaMemcpyDeviceToHost, s));
+          RRF_CUDA_TRY(cudaStreamSynchronize(s));
+          qi = qh;
+        } else if (opts->features_out != nullptr) {
+          RRF_CUDA_TRY(cudaMemcpyAsync(opts->features_out + 16 * (i - 1), w.feat, 16 * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s));
+          RRF_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (reorth && qi > 0) {  // the QR just computed gives the orthonormal start for free
+          RRF_CUDA_TRY(explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s));
+          start = w.Qt;
+        }
       }
+      if (opts != nullptr && opts->q_used_out != nullptr) opts->q_used_out[i - 1] = qi;
+      q_prev = qi;
+      RRF_CUDA_TRY(sketch_continue(r, c, b, T22, ldt, qi, bf16, reorth, start, w, s));
       // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
       RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,
                             w.hdr, s));
@@ -257,13 +310,13 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         double* CV = V + o * ldv;
         GemmDesc g1[2] = {gd(m, b, c, CT, ldt, 0, w.Yv, c, 0, w.Xa, m),
                           gd(n, b, c, CV, ldv, 0, w.Yv, c, 0, w.Xb, n)};
-        RRF_CUDA_TRY(gemm_f64(g1, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g1, 2, s));
         GemmDesc g2[2] = {gd(m, b, b, w.Xa, m, 0, w.Tv, b, 0, w.Xc, m),
                           gd(n, b, b, w.Xb, n, 0, w.Tv, b, 0, w.Xd, n)};
-        RRF_CUDA_TRY(gemm_f64(g2, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g2, 2, s));
         GemmDesc g3[2] = {gd(m, c, b, w.Xc, m, 0, w.Yv, c, 1, CT, ldt, -1.0, 1.0),
                           gd(n, c, b, w.Xd, n, 0, w.Yv, c, 1, CV, ldv, -1.0, 1.0)};
-        RRF_CUDA_TRY(gemm_f64(g3, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
       }
       // [U_i, R] = HQR_full(T(o:, o:o+b)).
       RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, w.Rs, b, w.panel, w.panel_bytes,
@@ -274,13 +327,13 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         const int64_t nc = c - b;
         GemmDesc g1[2] = {gd(b, nc, r, w.Yu, r, 1, C, ldt, 0, w.Wa, b),
                           gd(m, b, r, CU, ldu, 0, w.Yu, r, 0, w.Xa, m)};
-        RRF_CUDA_TRY(gemm_f64(g1, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g1, 2, s));
         GemmDesc g2[2] = {gd(b, nc, b, w.Tu, b, 1, w.Wa, b, 0, w.Wb, b),
                           gd(m, b, b, w.Xa, m, 0, w.Tu, b, 0, w.Xc, m)};
-        RRF_CUDA_TRY(gemm_f64(g2, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g2, 2, s));
         GemmDesc g3[2] = {gd(r, nc, b, w.Yu, r, 0, w.Wb, b, 0, C, ldt, -1.0, 1.0),
                           gd(m, r, b, w.Xc, m, 0, w.Yu, r, 1, CU, ldu, -1.0, 1.0)};
-        RRF_CUDA_TRY(gemm_f64(g3, 2, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
       }
       // SVD of R and the small updates.
       RRF_CUDA_TRY(jacobi_svd(b, w.Rs, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s));
@@ -294,7 +347,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
                          gd(n, b, b, VJ2, ldv, 0, w.Vs, b, 0, w.Xb, n),
                          gd(b, nc, b, w.Us, b, 1, TI2J3, ldt, 0, w.Wa, b),
                          gd(o, b, b, TI1J2, ldt, 0, w.Vs, b, 0, w.Xc, std::max<int64_t>(o, 1))};
-        RRF_CUDA_TRY(gemm_f64(g, o > 0 ? 4 : 3, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, g, o > 0 ? 4 : 3, s));
         RRF_CUDA_TRY(copy_matrix(m, b, w.Xa, m, UI2, ldu, s));
         RRF_CUDA_TRY(copy_matrix(n, b, w.Xb, n, VJ2, ldv, s));
         RRF_CUDA_TRY(copy_matrix(b, nc, w.Wa, b, TI2J3, ldt, s));
@@ -315,18 +368,18 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       double* CU = U + o * ldu;
       if (r > c) {  // U(:, o:) <- U(:, o:) (I - Yu Tu Yu^T)
         GemmDesc g1 = gd(m, c, r, CU, ldu, 0, w.Yu, r, 0, w.Xa, m);
-        RRF_CUDA_TRY(gemm_f64(&g1, 1, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, &g1, 1, s));
         GemmDesc g2 = gd(m, c, c, w.Xa, m, 0, w.Tu, c, 0, w.Xc, m);
-        RRF_CUDA_TRY(gemm_f64(&g2, 1, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, &g2, 1, s));
         GemmDesc g3 = gd(m, r, c, w.Xc, m, 0, w.Yu, r, 1, CU, ldu, -1.0, 1.0);
-        RRF_CUDA_TRY(gemm_f64(&g3, 1, w.gemm, w.gemm_bytes, s));
+        RRF_CUDA_TRY(gemm_run(w.eng, &g3, 1, s));
       }
       double* VJ = V + o * ldv;
       double* TI1J = T + o * ldt;
       GemmDesc g[3] = {gd(m, c, c, CU, ldu, 0, w.Us, c, 0, w.Xa, m),
                        gd(n, c, c, VJ, ldv, 0, w.Vs, c, 0, w.Xb, n),
                        gd(o, c, c, TI1J, ldt, 0, w.Vs, c, 0, w.Xc, std::max<int64_t>(o, 1))};
-      RRF_CUDA_TRY(gemm_f64(g, o > 0 ? 3 : 2, w.gemm, w.gemm_bytes, s));
+      RRF_CUDA_TRY(gemm_run(w.eng, g, o > 0 ? 3 : 2, s));
       RRF_CUDA_TRY(copy_matrix(m, c, w.Xa, m, CU, ldu, s));
       RRF_CUDA_TRY(copy_matrix(n, c, w.Xb, n, VJ, ldv, s));
       if (o > 0) RRF_CUDA_TRY(copy_matrix(o, c, w.Xc, o, TI1J, ldt, s));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -87,6 +88,27 @@ size_t gemm_scratch_bytes(const GemmDesc* d, int count);
 cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scratch_bytes,
                      cudaStream_t stream);
 
+// ---- FP64 GEMM emulated on the BF16 tensor cores (gemm_ozaki.cu) -------------------------------------
+bool ozaki_eligible(const GemmDesc& d, bool force);
+size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K);
+// d.M is the long side (>= 256); set out_transposed to write C^T (element (i, j) at C[j + i ldc]).
+cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, size_t scratch_bytes, int* status,
+                       cudaStream_t s);
+
+// Where the drivers send FP64 GEMMs: the DFMA kernel, or the emulation for the large ones.
+struct GemmEngine {
+  double* scratch = nullptr;  // DFMA split-K scratch
+  size_t scratch_bytes = 0;
+  char* oz = nullptr;         // emulation scratch (slices, exponents, split partials)
+  size_t oz_bytes = 0;
+  int* status = nullptr;
+  bool emulate = false;
+  bool force = false;  // emulate every eligible shape, not only large products
+};
+// Bytes of emulation scratch that cover every GEMM of a factorization of an m x n matrix with panel b.
+size_t ozaki_bound(int64_t m, int64_t n, int64_t b);
+cudaError_t gemm_run(const GemmEngine& eng, const GemmDesc* d, int count, cudaStream_t s);
+
 // ---- Gaussian generator (philox.cu) --------------------------------------------------------------
 cudaError_t randn_f64(int64_t rows, int64_t cols, double* G, int64_t ldg, uint64_t seed,
                       uint32_t step, uint32_t tag, cudaStream_t stream);
@@ -118,6 +140,12 @@ cudaError_t to_bf16(int64_t rows, int64_t cols, const double* S, int64_t lds, __
                     cudaStream_t s);
 cudaError_t to_bf16_t(int64_t rows, int64_t cols, const double* S, int64_t lds, __nv_bfloat16* D, int64_t ldd,
                       cudaStream_t s);
+
+// ---- learned q policy (mlp.cu) ------------------------------------------------------------------------
+// features of one step from the panel-factored q = 0 sketch (R on and above the diagonal of Rfac, ld ldr)
+cudaError_t policy_features(const double* Rfac, int64_t ldr, int b, const double* Y0, int64_t c, double* fro2_scratch,
+                            int step, int steps, int64_t n, int q_prev, float* feat, cudaStream_t s);
+cudaError_t policy_decide(const void* params, const float* feat, int* q_dev, cudaStream_t s);
 
 // ---- small kernels (aux.cu) ------------------------------------------------------------------------
 cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);

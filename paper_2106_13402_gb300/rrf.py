@@ -28,7 +28,9 @@ EXPORTED = [
     "rrf_jacobi_svd_workspace", "rrf_jacobi_svd", "rrf_workspace_status", "rrf_status_string",
     "rrf_last_arg_error", "rrf_version", "rrf_launch_count", "rrf_gemm_profile_begin", "rrf_gemm_profile_end",
     "rrf_gemm_bf16_workspace", "rrf_gemm_bf16", "rrf_batch_plan_create", "rrf_batch_plan_workspace",
-    "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32",
+    "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
+    "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
+    "rrf_gemm_emulated",
 ]
 
 
@@ -42,7 +44,14 @@ class RrfError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("sketch_prec", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("q_per_block", ctypes.POINTER(ctypes.c_int)), ("reserved", ctypes.c_int * 4)]
+                ("q_per_block", ctypes.POINTER(ctypes.c_int)), ("q_policy", ctypes.c_int),
+                ("mlp_params", ctypes.c_void_p), ("q_used_out", ctypes.POINTER(ctypes.c_int)),
+                ("features_out", ctypes.POINTER(ctypes.c_float)), ("gemm_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+Q_FIXED, Q_LEARNED = 0, 1
+GEMM_AUTO, GEMM_NATIVE, GEMM_EMULATED = 0, 1, 2
 
 
 _i64 = ctypes.c_int64
@@ -102,6 +111,19 @@ def lib():
             L.rrf_gemm_bf16.argtypes = [_i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz,
                                         _vp]
             L.rrf_gemm_bf16.restype = ctypes.c_int
+            L.rrf_gemm_emulated_workspace.argtypes = [_i64, _i64, _i64]
+            L.rrf_gemm_emulated_workspace.restype = _sz
+            L.rrf_gemm_emulated.argtypes = L.rrf_gemm.argtypes
+            L.rrf_gemm_emulated.restype = ctypes.c_int
+            L.rrf_mlp_param_count.restype = ctypes.c_int
+            L.rrf_mlp_train_workspace.argtypes = [ctypes.c_int]
+            L.rrf_mlp_train_workspace.restype = _sz
+            L.rrf_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
+            L.rrf_mlp_forward.restype = ctypes.c_int
+            L.rrf_mlp_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]
+            L.rrf_mlp_grad.restype = ctypes.c_int
+            L.rrf_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp]
+            L.rrf_mlp_adam.restype = ctypes.c_int
             L.rrf_batch_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                                 ctypes.POINTER(_i64), _i64, ctypes.c_int]
             L.rrf_batch_plan_create.restype = ctypes.c_int
@@ -164,16 +186,41 @@ def _check(st: int, what: str):
         raise RrfError(st, what)
 
 
-def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None):
+def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None, q_policy: int = Q_FIXED,
+              mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO):
+    """rrf_opts.  With q_policy=Q_LEARNED, pass `steps` (= ceil(n/b)) to receive per-step q and features in
+    opts.q_used / opts.features after the call; mlp_params is a CUDA float16 tensor of rrf_mlp_param_count
+    values (None: features only, q stays fixed)."""
     o = Opts()
     o.sketch_prec = int(sketch_prec)
     o.reorth = 1 if reorth else 0
-    keep = None
+    o.q_policy = int(q_policy)
+    o.gemm_mode = int(gemm_mode)
+    keep = []
     if q_per_block is not None:
-        keep = (ctypes.c_int * len(q_per_block))(*[int(v) for v in q_per_block])
-        o.q_per_block = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+        qa = (ctypes.c_int * len(q_per_block))(*[int(v) for v in q_per_block])
+        o.q_per_block = ctypes.cast(qa, ctypes.POINTER(ctypes.c_int))
+        keep.append(qa)
+    if mlp_params is not None:
+        o.mlp_params = mlp_params.data_ptr()
+        keep.append(mlp_params)
+    if steps > 0:
+        qu = (ctypes.c_int * steps)()
+        fo = (ctypes.c_float * (16 * steps))()
+        o.q_used_out = ctypes.cast(qu, ctypes.POINTER(ctypes.c_int))
+        o.features_out = ctypes.cast(fo, ctypes.POINTER(ctypes.c_float))
+        keep += [qu, fo]
+        o._qu, o._fo, o._steps = qu, fo, steps
     o._keep = keep
     return o
+
+
+def opts_q_used(o):
+    return [int(v) for v in o._qu]
+
+
+def opts_features(o):
+    return np.array(o._fo[:], dtype=np.float32).reshape(o._steps, 16)
 
 
 def workspace(nbytes: int, device="cuda"):
@@ -262,7 +309,10 @@ def randn(rows: int, cols: int, seed: int, step: int, tag: int, device="cuda", s
     return G
 
 
-def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None, stream=None):
+def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None, stream=None,
+         emulated: bool = False):
+    """C = alpha op(A) op(B) + beta C in FP64: the DFMA kernel (rrf_gemm) or the emulation on the BF16
+    tensor cores (rrf_gemm_emulated)."""
     L = lib()
     A = as_fortran(A)
     B = as_fortran(B)
@@ -272,13 +322,16 @@ def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, 
     if C is None:
         C = fortran_empty(m, n, A.device)
         C.zero_()
-    need = L.rrf_gemm_workspace(m, n, k)
+    need = L.rrf_gemm_emulated_workspace(m, n, k) if emulated else L.rrf_gemm_workspace(m, n, k)
     ws = workspace(need, A.device) if need else None
-    st = L.rrf_gemm(transa.encode(), transb.encode(), m, n, k, alpha, _vp(A.data_ptr()), _ld(A),
+    fn = L.rrf_gemm_emulated if emulated else L.rrf_gemm
+    st = fn(transa.encode(), transb.encode(), m, n, k, alpha, _vp(A.data_ptr()), _ld(A),
                     _vp(B.data_ptr()), _ld(B), beta, _vp(C.data_ptr()), _ld(C),
                     _vp(ws.data_ptr()) if ws is not None else None, ws.numel() if ws is not None else 0,
                     _stream(stream))
-    _check(st, "rrf_gemm")
+    _check(st, "rrf_gemm_emulated" if emulated else "rrf_gemm")
+    if emulated:
+        _check(L.rrf_workspace_status(_vp(ws.data_ptr()), _stream(stream)), "rrf_gemm_emulated (device status)")
     return C
 
 
@@ -354,6 +407,43 @@ def gemm_profile_end():
     if lib().rrf_gemm_profile_end(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)) != 0:
         raise RuntimeError("rrf_gemm_profile_end failed")
     return ms.value, fl.value, n.value
+
+
+def mlp_param_count() -> int:
+    return int(lib().rrf_mlp_param_count())
+
+
+def mlp_forward(params, X, stream=None):
+    """Logits (N x 4, FP32) of the policy MLP for features X (N x 16, FP32, CUDA)."""
+    torch = _torch()
+    X = X.contiguous().float()
+    N = X.shape[0]
+    out = torch.empty(N, 4, dtype=torch.float32, device=X.device)
+    _check(lib().rrf_mlp_forward(_vp(params.data_ptr()), _vp(X.data_ptr()), N, _vp(out.data_ptr()), _stream(stream)),
+           "rrf_mlp_forward")
+    return out
+
+
+def mlp_grad(params, X, labels, ws=None, stream=None):
+    """(gradient packed like the parameters, mean loss) of softmax cross-entropy over the samples."""
+    torch = _torch()
+    L = lib()
+    X = X.contiguous().float()
+    labels = labels.contiguous().to(torch.int32)
+    N = X.shape[0]
+    grad = torch.empty(mlp_param_count(), dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    need = L.rrf_mlp_train_workspace(N)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, X.device)
+    _check(L.rrf_mlp_grad(_vp(params.data_ptr()), _vp(X.data_ptr()), _vp(labels.data_ptr()), N, _vp(grad.data_ptr()),
+                          _vp(loss.data_ptr()), _vp(ws.data_ptr()), ws.numel(), _stream(stream)), "rrf_mlp_grad")
+    return grad, loss
+
+
+def mlp_adam(master, m, v, grad, params, step: int, lr: float, stream=None):
+    _check(lib().rrf_mlp_adam(_vp(master.data_ptr()), _vp(m.data_ptr()), _vp(v.data_ptr()), _vp(grad.data_ptr()),
+                              _vp(params.data_ptr()), step, lr, _stream(stream)), "rrf_mlp_adam")
 
 
 class BatchPlan:

@@ -396,3 +396,38 @@ def test_powerurv_theorem1_projectors(q):
         # error grows like eps * cond(W) (Sec. 3.2); the tolerance follows that bound.
         tol = max(1e-13, 100 * np.finfo(float).eps * np.linalg.cond(W))
         np.testing.assert_allclose(P1, P2, atol=tol * np.linalg.norm(A, 2))
+
+
+# ------------------------------------------------------------------------- policy MLP (FP64) --
+def _mlp_params(seed=0, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(5508) * scale
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """Backpropagation pinned by central differences of the loss (independent of the chain rule)."""
+    rng = np.random.default_rng(1)
+    p = _mlp_params(1)
+    X = rng.standard_normal((7, 16))
+    y = rng.integers(0, 4, 7)
+    loss, g = oracle.mlp_loss_grad(p, X, y)
+    idx = rng.choice(5508, 60, replace=False)
+    idx = np.concatenate([idx, [5504, 5507, 1024, 1087]])  # include biases
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle.mlp_loss_grad(pp, X, y)[0] - oracle.mlp_loss_grad(pm, X, y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_zero_network_closed_form():
+    """All-zero parameters: logits 0, loss log 4, only the output bias gets gradient mean(1/4 - onehot)."""
+    X = np.random.default_rng(2).standard_normal((8, 16))
+    y = np.array([0, 1, 2, 3, 0, 0, 1, 3])
+    loss, g = oracle.mlp_loss_grad(np.zeros(5508), X, y)
+    assert abs(loss - np.log(4.0)) < 1e-15
+    expect = np.array([0.25 - np.mean(y == k) for k in range(4)])
+    np.testing.assert_allclose(g[-4:], expect, atol=1e-15)
+    assert np.all(g[:-4] == 0.0)
