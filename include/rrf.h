@@ -175,14 +175,13 @@ RRF_API rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, int6
 
 /* FP64 GEMM emulated on the BF16 tensor cores (error-free splitting, Ozaki et al. 2012): same arguments and
  * result convention as rrf_gemm.  Each row of op(A) and column of op(B) is scaled by a power of two and split
- * into 7 signed 8-bit digits (exact in BF16; remainder below 2^-56 of the row / column maximum); the 28
- * digit products of each 32-wide K chunk accumulate exactly in FP32 on tcgen05 and are folded into a
- * double-float and then an FP64 accumulator.  The error is measured relative to the row and column maxima,
- * not to (|op(A)||op(B)|)_ij: |error_ij| <~ 2K 2^-53 (|op(A)||op(B)|)_ij + 2^-46 K max_k|a_ik| max_k|b_kj|
- * (worst case; random signs give about 2^-47.5 sqrt(K) max|a_i.| max|b_.j|), so entries far below their
- * row / column scale lose relative accuracy that the native FP64 GEMM keeps.
- * Needs max(m, n) >= 128, min(m, n) >= 64,
- * k >= 32, and rrf_gemm_emulated_workspace(m, n, k) bytes of workspace. */
+ * into 7 signed 8-bit digits (exact in BF16; remainder below 2^-55 of the row / column maximum); the digit
+ * products of each 32-wide K chunk accumulate exactly in FP32 on tcgen05 and then exactly in an int64 per
+ * output; only digit products below 2^-56 of the scale are dropped.  Error relative to the row and column
+ * maxima: |error_ij| <~ 2^-53 |C_ij| + 2^-51.4 K max_k|a_ik| max_k|b_kj| (worst case; random digits give
+ * about 2^-55 sqrt(K) max|a_i.| max|b_.j|), so entries far below their row / column scale lose relative
+ * accuracy that the native FP64 GEMM keeps.  Needs max(m, n) >= 128, min(m, n) >= 64, k >= 32, and
+ * rrf_gemm_emulated_workspace(m, n, k) bytes of workspace. */
 RRF_API size_t rrf_gemm_emulated_workspace(int64_t m, int64_t n, int64_t k);
 RRF_API rrf_status rrf_gemm_emulated(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
@@ -214,7 +213,9 @@ RRF_API rrf_status rrf_panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, do
  * largest-magnitude entry is positive.  Columns with s_k = 0 get u_k by Gram-Schmidt completion.
  * The rotation rule and stopping test are those of Hestenes' method with tolerance c * 2^-53;
  * the column pairs follow a round-robin (tournament) ordering.  Status (converged or not) goes to
- * the workspace status word. */
+ * the workspace status word.  For 32 <= c <= 128 with rrf_jacobi_svd_workspace(c) bytes, FP32 sweeps
+ * first give a starting V (made orthogonal in FP64 by two Newton-Schulz steps) and the FP64 sweeps run
+ * on M V from there; a workspace of just the header size runs the FP64 sweeps from V = I. */
 RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
 RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                           double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream);

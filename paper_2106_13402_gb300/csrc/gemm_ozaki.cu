@@ -3,21 +3,26 @@
 // multiplication and its applications", Numer. Algorithms 2012), for the compact-WY updates and sketch
 // products of Algorithms 1 and 3 on a GPU whose FP64 units are ~1/1600 of its BF16 tensor throughput.
 //
-// Splitting: row r of op(A) (length K) is scaled by 2^-e_r, where 2^e_r bounds its largest magnitude, and
-// written as S = 7 signed 8-bit digits per entry:  a = 2^e_r sum_s d_s 2^-8(s+1),  |d_0| <= 256,
-// |d_s| <= 128 -- every digit an exact BF16 value and every step exact in FP64; the dropped remainder is
-// below 2^-56 of the row maximum.  Columns of op(B) likewise (exponents f_c).
-// Products: sum_k d^A_i d^B_j over a 32-wide K chunk is an integer below 32 * 2^16 = 2^21, so the
-// tcgen05 MMA's FP32 accumulation is exact, and the up to 7 pairs (i, j) of one diagonal i + j = d fit
-// below 2^24 in one TMEM accumulator per diagonal.  After each chunk the 7 diagonal sums are folded into a
-// double-float (hi, lo) FP32 accumulator per output (error-free two-sum for the three leading diagonals,
-// a Horner sum of the rest, whose weight is below 2^-24 of the total, into lo), and every 16 chunks the
-// pair moves into an FP64 accumulator.  C = alpha 2^(e_r + f_c - 16) acc + beta C in FP64 at the end.
+// Splitting: row r of op(A) (length K) is scaled by 2^-e_r, where max_k |a_rk| < 2^(e_r - 1), and written
+// as S = 7 signed base-256 digits per entry:  a = 2^e_r sum_s d_s 2^-8(s+1) + rem,  |d_s| <= 128,
+// |rem| <= 2^-57 2^e_r < 2^-55 max_k |a_rk| -- every digit an exact BF16 value and every step exact in FP64.
+// Columns of op(B) likewise (exponents f_c).
+// Products: a digit product is at most 2^14, so over a 32-wide K chunk the diagonal sum
+// S_d = sum_{i+j=d} sum_k d^A_i d^B_j (d + 1 pairs) is an integer of magnitude <= (d + 1) 2^19 <= 2^22: the
+// tcgen05 MMA's FP32 accumulation is exact, and so is the conversion of each S_d to an integer (x + 1.5 2^23
+// holds round(x) in its low mantissa bits).  The epilogue adds S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4
+// into one int64 per output (exact; a split covers at most 65536 of K, so it stays below 2^63) and the
+// remaining S_5 2^-8 + S_6 2^-16 into an FP32 fraction whose integer part moves into the int64 after every
+// chunk (its rounding is below 2^-60 of the row/column scale per chunk).  The digit products of diagonals
+// 7..12 are dropped (at most 2^-51.4 max|a_r.| max|b_.c| per k, ~2^-56 for random digits).  At the end
+// C = alpha 2^(e_r + f_c - 48) (acc + frac) + beta C in FP64.
 //
-// Kernel roles (320 threads): warp 0 lane 0 loads 7 + 7 slice tiles per 32-wide K chunk with TMA (64-byte
-// swizzle, 2-stage ring); warp 1 lane 0 issues 56 MMAs (28 pairs x two K = 16 halves) per chunk into 7
-// TMEM accumulators of 64 columns; warps 2..9 read the accumulators (tcgen05.ld) and fold them.  All
-// mbarrier waits are bounded (RRF_TIMEOUT, drain, free TMEM, exit).
+// Kernel (320 threads, persistent over 128 x 32 output tiles x K splits): warp 0 lane 0 loads the 7 + 7
+// digit tiles of each 32-wide K chunk with TMA (64-byte swizzle, 3-stage ring); warp 1 lane 0 issues, per
+// 16-wide K step and A digit a, one MMA of A_a against the B digits 0..6-a laid back to back (N = (7-a) 32),
+// into two TMEM accumulator buffers of 7 x 32 columns used alternately; warps 2..9 read a buffer
+// (tcgen05.ld) while the MMAs fill the other.  All mbarrier waits are bounded (RRF_TIMEOUT, drain, free
+// TMEM, exit).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -30,28 +35,54 @@ namespace rrf {
 namespace {
 
 constexpr int kS = 7;            // digits per value
-constexpr int BM = 128, BN = 64;
+constexpr int BM = 128, BN = 32;
 constexpr int KC = 32;           // K per chunk / stage (64 bytes of BF16: 64-byte swizzle)
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
+constexpr int kBufCols = 256;    // TMEM columns between the two accumulator buffers (7 x BN = 224 used)
+constexpr int kGroupM = 8;       // tile raster: groups of 8 row tiles, column tiles fastest inside a group
+constexpr int64_t kMaxSplitK = 65536;  // K of one split: keeps the int64 accumulator below 2^63
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr uint32_t kTileA = BM * KC * 2;   // 8 KB per slice
-constexpr uint32_t kTileB = BN * KC * 2;   // 4 KB per slice
+constexpr uint32_t kTileB = BN * KC * 2;   // 2 KB per slice
 constexpr uint32_t kStageBytes = kS * (kTileA + kTileB);
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: x + kMagic holds round(x) in its low bits, |x| <= 2^22
+constexpr int kMagicBits = 0x4B400000;
 
 struct OzParams {
   int64_t M, N, Kp;     // Kp: padded K (multiple of KC)
-  int64_t kchunk;       // K per split (multiple of KC)
+  int64_t kchunk;       // K per split (multiple of KC, <= kMaxSplitK)
+  int64_t units;        // tiles_m * tiles_n * splits
+  int tiles_m, tiles_n, splits;
   const int* ea;        // M row exponents
   const int* eb;        // N column exponents
   double alpha, beta;
   double* C;            // splits == 1: C (ldc); else partials [split][N][M]
   int64_t ldc;
-  int splits;
   int ct;               // write C^T: element (row, col) at C[col + row ldc]
   int* status;
 };
+
+// Work unit u -> (row tile, column tile, split).  Splits outermost; inside a split, groups of kGroupM row
+// tiles with the column tile varying fastest, so the CTAs resident at one time share digit tiles in L2.
+__device__ __forceinline__ void unit_coords(const OzParams& p, int64_t u, int64_t& m0, int64_t& n0, int& split) {
+  const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
+  split = (int)(u / tiles);
+  const int64_t t = u - (int64_t)split * tiles;
+  const int64_t per_group = (int64_t)kGroupM * p.tiles_n;
+  const int64_t first = (t / per_group) * kGroupM;
+  const int64_t gm = min((int64_t)kGroupM, (int64_t)p.tiles_m - first);
+  const int64_t r = t % per_group;
+  m0 = (first + r % gm) * BM;
+  n0 = (r / gm) * BN;
+}
+
+__device__ __forceinline__ int unit_chunks(const OzParams& p, int split, int64_t& k0) {
+  k0 = (int64_t)split * p.kchunk;
+  const int64_t k1 = min(p.Kp, k0 + p.kchunk);
+  return k1 > k0 ? (int)((k1 - k0) / KC) : 0;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -112,6 +143,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Exact integer value of a TMEM word holding an integer-valued FP32 x with |x| <= 2^22.
+__device__ __forceinline__ int exact_int(uint32_t bits) {
+  return __float_as_int(__fadd_rn(__uint_as_float(bits), kMagic)) - kMagicBits;
+}
+
+// Persistent kernel: each CTA walks work units blockIdx.x, blockIdx.x + gridDim.x, ...  The 32-wide K
+// chunks of all its units form one stream g = 0, 1, ...: chunk g uses smem stage g % kStages and TMEM
+// accumulator buffer g % 2, so the MMAs of chunk g + 1 run while the epilogue folds chunk g.
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                       const __grid_constant__ OzParams p) {
@@ -119,25 +158,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
-  __shared__ __align__(8) uint64_t acc_full;
-  __shared__ __align__(8) uint64_t acc_empty;
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-  const int split = blockIdx.z;
-  const int64_t k0 = (int64_t)split * p.kchunk;
-  const int64_t k1 = min(p.Kp, k0 + p.kchunk);
-  const int nch = k1 > k0 ? (int)((k1 - k0) / KC) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -152,154 +188,162 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  int issued = 0;
+  int64_t issued = 0;
   if (warp == 0) {
     if (lane == 0) {
-      for (int i = 0; i < nch; ++i) {
-        const int s = i % kStages;
-        if (i >= kStages && !mbar_wait(&empty_bar[s], ((i / kStages) - 1) & 1)) {
-          set_status(p.status, RRF_TIMEOUT);
-          atomicExch(&abort_flag, 1);
-          break;
+      int64_t g = 0;
+      bool run = true;
+      for (int64_t u = blockIdx.x; u < p.units && run; u += gridDim.x) {
+        int64_t m0, n0, k0;
+        int split;
+        unit_coords(p, u, m0, n0, split);
+        const int nch = unit_chunks(p, split, k0);
+        for (int i = 0; i < nch; ++i, ++g) {
+          const int s = (int)(g % kStages);
+          if (g >= kStages && !mbar_wait(&empty_bar[s], (uint32_t)((g / kStages) - 1) & 1)) {
+            set_status(p.status, RRF_TIMEOUT);
+            atomicExch(&abort_flag, 1);
+            run = false;
+            break;
+          }
+          if (*(volatile int*)&abort_flag) { run = false; break; }
+          unsigned char* st = smem + s * kStageBytes;
+          mbar_expect_tx(&full_bar[s], kStageBytes);
+          const int kx = (int)(k0 + (int64_t)i * KC);
+          for (int sl = 0; sl < kS; ++sl) {
+            tma_load_2d(st + sl * kTileA, &map_a, &full_bar[s], kx, (int)(sl * p.M + m0));
+            tma_load_2d(st + kS * kTileA + sl * kTileB, &map_b, &full_bar[s], kx, (int)(sl * p.N + n0));
+          }
+          issued = g + 1;
         }
-        if (*(volatile int*)&abort_flag) break;
-        unsigned char* st = smem + s * kStageBytes;
-        mbar_expect_tx(&full_bar[s], kStageBytes);
-        const int kx = (int)(k0 + (int64_t)i * KC);
-        for (int sl = 0; sl < kS; ++sl) {
-          tma_load_2d(st + sl * kTileA, &map_a, &full_bar[s], kx, (int)(sl * p.M + m0));
-          tma_load_2d(st + kS * kTileA + sl * kTileB, &map_b, &full_bar[s], kx, (int)(sl * p.N + n0));
-        }
-        ++issued;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-      for (int i = 0; i < nch; ++i) {
-        const int s = i % kStages;
-        if (!mbar_wait(&full_bar[s], (i / kStages) & 1) || (i > 0 && !mbar_wait(&acc_empty, (i - 1) & 1))) {
+      // One MMA per A digit a per 16-wide K step: D[a .. 6] += A_a [B_0 .. B_{6-a}]^T.  The B digit tiles sit
+      // back to back in shared memory, so they form one K-major operand of N = (7 - a) BN rows whose
+      // products land on the diagonals a + j, stored contiguously in TMEM (diagonal d at column d BN).
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
+      int64_t g = 0;
+      bool run = true;
+      for (int64_t u = blockIdx.x; u < p.units && run; u += gridDim.x) {
+        int64_t m0, n0, k0;
+        int split;
+        unit_coords(p, u, m0, n0, split);
+        const int nch = unit_chunks(p, split, k0);
+        for (int i = 0; i < nch; ++i, ++g) {
+          const int s = (int)(g % kStages);
+          const int bf = (int)(g & 1);
+          if (!mbar_wait(&full_bar[s], (uint32_t)(g / kStages) & 1) ||
+              (g >= 2 && !mbar_wait(&acc_empty[bf], (uint32_t)((g >> 1) - 1) & 1))) {
+            set_status(p.status, RRF_TIMEOUT);
+            atomicExch(&abort_flag, 1);
+            run = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* st = smem + s * kStageBytes;
+          const uint64_t db = smem_desc_sw64(st + kS * kTileA);
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk) {
+#pragma unroll
+            for (int a = 0; a < kS; ++a) {
+              const uint64_t da = smem_desc_sw64(st + a * kTileA);
+              const uint32_t idesc = idesc0 | ((uint32_t)(((kS - a) * BN) >> 3) << 17);
+              mma_bf16(tmem + (uint32_t)(bf * kBufCols + a * BN), da + 2 * kk, db + 2 * kk, idesc,
+                       (a > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty_bar[s]);
+          mma_commit(&acc_full[bf]);
+        }
+      }
+      // the last MMAs must finish before TMEM is released
+      if (g > 0) mbar_wait(&acc_full[(g - 1) & 1], (uint32_t)((g - 1) >> 1) & 1);
+    }
+  } else {
+    // Epilogue warps ew = 0..7: TMEM lane quadrant (warp % 4) = 32 tile rows, columns 16 (ew / 4) .. +15.
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int col0 = (ew >> 2) * 16;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+    int64_t g = 0;
+    for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+      int64_t m0, n0, k0;
+      int split;
+      unit_coords(p, u, m0, n0, split);
+      const int nch = unit_chunks(p, split, k0);
+      // acc: sum over chunks of S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 (exact); ta: the rest,
+      // S_5 2^-8 + S_6 2^-16, in the same unit, with its integer part moved into acc after every chunk.
+      long long acc[16];
+      float ta[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) { acc[c] = 0; ta[c] = 0.f; }
+      bool ok = true;
+      for (int i = 0; i < nch; ++i, ++g) {
+        const int bf = (int)(g & 1);
+        if (!mbar_wait(&acc_full[bf], (uint32_t)(g >> 1) & 1)) {
           set_status(p.status, RRF_TIMEOUT);
           atomicExch(&abort_flag, 1);
+          ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* st = smem + s * kStageBytes;
-        for (int d = 0; d < kS; ++d) {
-          for (int a = 0; a <= d; ++a) {
-            const uint64_t da = smem_desc_sw64(st + a * kTileA);
-            const uint64_t db = smem_desc_sw64(st + kS * kTileA + (d - a) * kTileB);
 #pragma unroll
-            for (int kk = 0; kk < KC / 16; ++kk)
-              mma_bf16(tmem + (uint32_t)(d * BN), da + 2 * kk, db + 2 * kk, idesc, (a > 0 || kk > 0) ? 1u : 0u);
+        for (int h = 0; h < 16; h += 8) {
+          uint32_t v[kS][8];
+#pragma unroll
+          for (int d = 0; d < kS; ++d) tmem_ld8(trow + (uint32_t)(bf * kBufCols + d * BN + h), v[d]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            // |S_d| <= (d + 1) 32 2^14 <= 2^22 for every diagonal: each converts exactly.
+            const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^28
+            const int mid = exact_int(v[2][c]) * 256 + exact_int(v[3][c]);  // |.| < 2^30
+            float t = fmaf(__uint_as_float(v[5][c]), 0.00390625f, ta[h + c]);
+            t = fmaf(__uint_as_float(v[6][c]), 1.52587890625e-05f, t);
+            const float r = __fadd_rn(t, kMagic);
+            const int ti = __float_as_int(r) - kMagicBits;
+            ta[h + c] = __fsub_rn(t, __fsub_rn(r, kMagic));
+            acc[h + c] += (long long)hi * 16777216LL + (long long)mid * 256LL + (long long)(exact_int(v[4][c]) + ti);
           }
         }
-        mma_commit(&empty_bar[s]);
-        mma_commit(&acc_full);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[bf]);
       }
-    }
-  } else {
-    // Epilogue warps: ew 0..7; lanes 32 (ew % 4) .. of TMEM = tile rows, column half (ew / 4).
-    const int ew = warp - 2;
-    const int quad = warp & 3;        // TMEM lane quadrant this warp may access
-    const int col0 = (ew / 4) * 32;   // 32 of the 64 columns
-    float hi[32], lo[32];
-    double acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) { hi[c] = 0.f; lo[c] = 0.f; acc[c] = 0.0; }
-    bool ok = true;
-    for (int i = 0; i < nch && ok; ++i) {
-      if (!mbar_wait(&acc_full, i & 1)) {
-        set_status(p.status, RRF_TIMEOUT);
-        atomicExch(&abort_flag, 1);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int cc = 0; cc < 32; cc += 8) {
-        uint32_t v[kS][8];
-#pragma unroll
-        for (int d = 0; d < kS; ++d)
-          tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(d * BN + col0 + cc), v[d]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          // Diagonals 0..2 enter the double-float (hi, lo) through an error-free two-sum; diagonals 3..6
-          // (weight <= 2^-24 of the total) are folded by Horner and added to lo.
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const float x = __uint_as_float(v[d][c]) * (d == 0 ? 1.f : (d == 1 ? 0.00390625f : 1.52587890625e-05f));
-            const float sm = hi[cc + c] + x;
-            const float bb = sm - hi[cc + c];
-            const float err = (hi[cc + c] - (sm - bb)) + (x - bb);
-            hi[cc + c] = sm;
-            lo[cc + c] += err;
-          }
-          float tail = 0.f;
-#pragma unroll
-          for (int d = kS - 1; d >= 3; --d) tail = fmaf(tail, 0.00390625f, __uint_as_float(v[d][c]));
-          lo[cc + c] = fmaf(tail, 5.9604644775390625e-08f, lo[cc + c]);  // tail * 2^-24
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty);
-      // every 16 chunks (and at the end) move the double-float into an FP64 accumulator
-      if ((i & 15) == 15 || i == nch - 1) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          acc[c] += (double)hi[c] + (double)lo[c];
-          hi[c] = 0.f;
-          lo[c] = 0.f;
-        }
-      }
-    }
-    if (ok && nch > 0 && *(volatile int*)&abort_flag == 0) {
+      if (!ok || *(volatile int*)&abort_flag) break;
       const int64_t row = m0 + quad * 32 + lane;
-      if (row < p.M) {
-        const int er = p.ea[row];
-#pragma unroll 4
-        for (int c = 0; c < 32; ++c) {
-          const int64_t col = n0 + col0 + c;
-          if (col >= p.N) break;
-          const double v = ldexp(acc[c], er + p.eb[col] - 16);
-          if (p.splits == 1) {
-            double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
-            double out = p.alpha * v;
-            if (p.beta != 0.0) out = fma(p.beta, *cp, out);
-            *cp = out;
-          } else {
-            p.C[((int64_t)split * p.N + col) * p.M + row] = v;
-          }
+      if (row >= p.M) continue;
+      const int er = p.ea[row];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int64_t col = n0 + col0 + c;
+        if (col >= p.N) continue;
+        // value = 2^(e_r + f_c) sum_d S_d 2^-8(d+2) = (acc + ta) 2^(e_r + f_c - 48)
+        const double v = nch > 0 ? ldexp((double)acc[c] + (double)ta[c], er + p.eb[col] - 48) : 0.0;
+        if (p.splits == 1) {
+          double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
+          double out = p.alpha * v;
+          if (p.beta != 0.0) out = fma(p.beta, *cp, out);
+          *cp = out;
+        } else {
+          p.C[((int64_t)split * p.N + col) * p.M + row] = v;
         }
       }
-    } else if (nch == 0) {
-      const int64_t row = m0 + quad * 32 + lane;
-      if (row < p.M)
-        for (int c = 0; c < 32; ++c) {
-          const int64_t col = n0 + col0 + c;
-          if (col >= p.N) break;
-          if (p.splits == 1) {
-            double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
-            *cp = (p.beta != 0.0) ? p.beta * *cp : 0.0;
-          } else {
-            p.C[((int64_t)split * p.N + col) * p.M + row] = 0.0;
-          }
-        }
     }
   }
   __syncthreads();
   if (abort_flag && warp == 0 && lane == 0)
-    for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
-      mbar_wait(&full_bar[i % kStages], (i / kStages) & 1);
+    for (int64_t i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+      mbar_wait(&full_bar[i % kStages], (uint32_t)(i / kStages) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
 }
 
-// Row exponents: e_r with max_k |X(r, k)| < 2^e_r (0 for an all-zero row).  X(r, k) = X[r sr + k sk].
+// Row exponents: e_r with max_k |X(r, k)| < 2^(e_r - 1) (0 for an all-zero row).  X(r, k) = X[r sr + k sk].
 __global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restrict__ X, int64_t sr, int64_t sk,
                                  int* __restrict__ e) {
   if (sr == 1) {  // rows contiguous in memory across threads
@@ -308,7 +352,7 @@ __global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restri
       for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(X[r + k * sk]));
       int ex = 0;
       if (mx > 0.0) frexp(mx, &ex);
-      e[r] = ex;
+      e[r] = mx > 0.0 ? ex + 1 : 0;
     }
   } else {  // each row contiguous: one warp per row
     const int lane = threadIdx.x & 31;
@@ -322,7 +366,7 @@ __global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restri
       if (lane == 0) {
         int ex = 0;
         if (mx > 0.0) frexp(mx, &ex);
-        e[r] = ex;
+        e[r] = mx > 0.0 ? ex + 1 : 0;
       }
     }
   }
@@ -405,8 +449,8 @@ int oz_splits(int64_t M, int64_t N, int64_t Kp) {
   const int sms = dev_info().sms;
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int64_t chunks = Kp / KC;
-  int s = 1;
-  while (tiles * s * 2 <= 2 * sms && chunks / (s * 2) >= 8 && s < 16) s *= 2;
+  int s = (int)((Kp + kMaxSplitK - 1) / kMaxSplitK);
+  while (tiles * s < sms && chunks / (s * 2) >= 8 && s < 64) s *= 2;
   return s;
 }
 
@@ -499,14 +543,17 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   OzParams p;
   p.M = M; p.N = N; p.Kp = Kp;
   p.kchunk = ((Kp / KC + splits - 1) / splits) * KC;
+  p.tiles_m = (int)((M + BM - 1) / BM);
+  p.tiles_n = (int)((N + BN - 1) / BN);
+  p.splits = splits;
+  p.units = (int64_t)p.tiles_m * p.tiles_n * splits;
   p.ea = ea; p.eb = eb;
   p.alpha = d.alpha; p.beta = d.beta;
-  p.splits = splits;
   p.C = splits == 1 ? d.C : part;
   p.ldc = d.ldc;
   p.ct = out_transposed ? 1 : 0;
   p.status = status;
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+  const unsigned grid = (unsigned)std::min<int64_t>(p.units, sms);
   ozaki_gemm_kernel<<<grid, kThreads, oz_smem(), s>>>(ma, mb, p);
   count_launch();
   cudaError_t e = cudaGetLastError();

@@ -72,7 +72,11 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& 
   w.fro2 = ar.take<double>(4);
   w.panel_bytes = panel_scratch_bytes(mx, b);
   w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
-  w.gemm_bytes = (size_t)16 * mx * b * sizeof(double);
+  // split-K partials of the DFMA GEMMs; between them it also serves as the small SVD's scratch
+  const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
+  const int64_t c_last = std::min(b, n - (steps - 1) * b);
+  w.gemm_bytes = std::max({(size_t)16 * mx * b * sizeof(double), jacobi_scratch_bytes(std::min(b, n)),
+                           jacobi_scratch_bytes(c_last)});
   w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
   w.eng.scratch = w.gemm;
   w.eng.scratch_bytes = w.gemm_bytes;
@@ -336,7 +340,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
       }
       // SVD of R and the small updates.
-      RRF_CUDA_TRY(jacobi_svd(b, w.Rs, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s));
+      RRF_CUDA_TRY(jacobi_svd(b, w.Rs, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s, w.gemm, w.gemm_bytes));
       {
         const int64_t nc = c - b;
         double* UI2 = U + o * ldu;
@@ -364,7 +368,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         M = w.Rs;
         ldm = c;
       }
-      RRF_CUDA_TRY(jacobi_svd(c, M, ldm, w.Us, c, w.sig, w.Vs, c, w.hdr, s));
+      RRF_CUDA_TRY(jacobi_svd(c, M, ldm, w.Us, c, w.sig, w.Vs, c, w.hdr, s, w.gemm, w.gemm_bytes));
       double* CU = U + o * ldu;
       if (r > c) {  // U(:, o:) <- U(:, o:) (I - Yu Tu Yu^T)
         GemmDesc g1 = gd(m, c, r, CU, ldu, 0, w.Yu, r, 0, w.Xa, m);

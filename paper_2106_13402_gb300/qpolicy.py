@@ -102,16 +102,20 @@ def label_matrix(A, s, b: int, seed: int, target: float = 1.1, qmax: int = 3):
 
 
 def generate(count: int, n: int, b: int, seed0: int = 1000, log=None):
-    X, y = [], []
+    """Features, labels, e_k for q = 0..3 and sigma_{k+1} of every step of `count` seeded matrices."""
+    X, y, E, S = [], [], [], []
     t0 = time.time()
     for t in range(count):
         A, sv = make_matrix(n, seed0 + t)
-        f, lab, _ = label_matrix(A, sv, b, seed0 + t)
+        f, lab, errs = label_matrix(A, sv, b, seed0 + t)
         X.append(f)
         y.append(lab)
+        E.append(errs.T)
+        S.append(np.asarray(sv)[b * np.arange(1, f.shape[0] + 1)])
         if log and (t + 1) % 25 == 0:
             log(f"  {t + 1}/{count} matrices labelled, {time.time() - t0:.0f} s")
-    return np.concatenate(X).astype(np.float32), np.concatenate(y).astype(np.int32)
+    return (np.concatenate(X).astype(np.float32), np.concatenate(y).astype(np.int32), np.concatenate(E),
+            np.concatenate(S))
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -172,11 +176,14 @@ def main():
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--data-only", action="store_true")
     a = ap.parse_args()
     print(f"labelling {a.count} matrices of {a.n}^2 (b = {a.b})", flush=True)
-    X, y = generate(a.count, a.n, a.b, log=lambda s: print(s, flush=True))
+    X, y, E, S = generate(a.count, a.n, a.b, log=lambda s: print(s, flush=True))
     print("label histogram q=0..3:", np.bincount(y, minlength=4).tolist(), flush=True)
-    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y)
+    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, E=E, S=S)
+    if a.data_only:
+        return
     params = train(X, y, epochs=a.epochs, log=lambda s: print(s, flush=True))
     save(params, a.out)
     print("saved", a.out, flush=True)

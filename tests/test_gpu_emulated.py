@@ -1,13 +1,13 @@
 """FP64 GEMM emulated on the BF16 tensor cores, and both factorizations running on it.
 
 The emulation splits each row of op(A) / column of op(B) into 7 exact 8-bit digits below a power-of-two
-scale (remainder < 2^-56 of the row / column maximum) and accumulates the digit products exactly in
-FP32 per 32-wide K chunk, then in double-float (about 2^-47 relative to the running digit sum) and FP64.
-The digit sums live on the scale of the row / column maxima, so against an extended-precision reference
-(numpy longdouble) each entry is held to the FP64 GEMM bound 2 K 2^-53 (|op(A)||op(B)|)_ij plus the
-worst-case double-float and truncation term 2^-46 K max_k|a_ik| max_k|b_kj|; a second check holds the
-typical error (random signs) to 2^-45 sqrt(K) max|a_i.| max|b_.j|, which dropping any digit diagonal
-but the last (diagonal d weighs up to (d + 1) 2^-8d of the scale per product) fails.  The factorizations keep every FP64 tolerance of the native path.
+scale (remainder < 2^-55 of the row / column maximum), accumulates the digit products exactly (FP32 on the
+tensor cores per 32-wide K chunk, then int64) and drops only the digit products of diagonals 7..12 (at most
+2^-51.4 of the row / column scale per k).  Against an extended-precision reference (numpy longdouble) each
+entry is held to 2^-51 (|alpha op(A) op(B)| + |beta C|)_ij for the final FP64 roundings plus the worst case
+2^-50 K max_k|a_ik| max_k|b_kj| of the dropped digits; a second check holds the typical error (random
+digits, about 2^-55 sqrt(K) of the scale) to 2^-51 sqrt(K) max|a_i.| max|b_.j|, which an accumulation that
+rounds at 2^-48 per chunk fails.  The factorizations keep every FP64 tolerance of the native path.
 """
 import numpy as np
 import pytest
@@ -35,7 +35,8 @@ def dev(x):
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("m,n,k,graded", [(128, 64, 32, False), (300, 100, 1000, False), (513, 200, 77, True),
-                                          (64, 300, 500, False), (600, 256, 2048, True)])
+                                          (64, 300, 500, False), (600, 256, 2048, True),
+                                          (1024, 640, 96, False), (256, 64, 8192, False)])
 def test_emulated_gemm_accuracy(ta, tb, m, n, k, graded):
     rng = np.random.default_rng(m + 3 * n + 7 * k)
     A = rng.standard_normal((k, m) if ta == "T" else (m, k))
@@ -50,11 +51,12 @@ def test_emulated_gemm_accuracy(ta, tb, m, n, k, graded):
     ref = (-0.75 * (opA.astype(L) @ opB.astype(L)) + 0.5 * C0.astype(L)).astype(np.float64)
     absA, absB = np.abs(opA), np.abs(opB)
     scale = np.outer(absA.max(axis=1), absB.max(axis=0))
-    bound = 0.75 * (2 * k * EPS * (absA @ absB) + 2.0 ** -46 * k * scale)
-    bound += 2 * EPS * 0.5 * np.abs(C0) + 1e-300
+    prod = np.abs((opA.astype(L) @ opB.astype(L)).astype(np.float64))
+    rnd = 2.0 ** -51 * (0.75 * prod + 0.5 * np.abs(C0))
     err = np.abs(C - ref)
+    bound = rnd + 0.75 * 2.0 ** -50 * k * scale + 1e-300
     assert np.all(err <= bound), float((err / bound).max())
-    typical = 0.75 * 2.0 ** -45 * np.sqrt(k) * scale + 2 * EPS * 0.5 * np.abs(C0) + 1e-300
+    typical = rnd + 0.75 * 2.0 ** -51 * np.sqrt(k) * scale + 1e-300
     assert np.all(err <= typical), float((err / typical).max())
 
 
