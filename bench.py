@@ -45,7 +45,21 @@ def parse():
     p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=2, help="randUTV steps the oracle runs per sample")
     p.add_argument("--methods", default="randutv,powerurv", help="comma list (profiling runs may time one)")
+    p.add_argument("--gemm", default="auto", choices=["auto", "native", "emulated"],
+                   help="FP64 products: library default, DFMA only, or emulated on the BF16 tensor cores")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 (DFMA) comparison run")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                   help="c2: FP64 randUTV + powerURV 8192^2 (default); c3: BF16-sketch randUTV 16384^2, b=256, q=2; "
+                        "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128")
     return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 # ------------------------------------------------------------------------------------ clock sampling --
@@ -172,17 +186,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     outs = {name: (rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev))
             for name in ("randutv", "powerurv")}
-    wss = {"randutv": rrf.workspace(rrf.randutv_workspace_bytes(n, n, b), dev),
-           "powerurv": rrf.workspace(rrf.powerurv_workspace_bytes(n, n, b), dev)}
     stream = torch.cuda.current_stream()
 
     methods = [x for x in args.methods.split(",") if x]
+    gemm_mode = {"auto": rrf.GEMM_AUTO, "native": rrf.GEMM_NATIVE, "emulated": rrf.GEMM_EMULATED}[args.gemm]
+    opts = rrf.make_opts(gemm_mode=gemm_mode)
+    wss = {"randutv": rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, opts), dev),
+           "powerurv": rrf.workspace(rrf.powerurv_workspace_bytes(n, n, b, opts), dev)}
 
     def step():
         if "randutv" in methods:
-            rrf.randutv(A, b, q, seed=17, out=outs["randutv"], ws=wss["randutv"], check_status=False)
+            rrf.randutv(A, b, q, seed=17, opts=opts, out=outs["randutv"], ws=wss["randutv"], check_status=False)
         if "powerurv" in methods:
-            rrf.powerurv(A, b, q, seed=17, out=outs["powerurv"], ws=wss["powerurv"], check_status=False)
+            rrf.powerurv(A, b, q, seed=17, opts=opts, out=outs["powerurv"], ws=wss["powerurv"], check_status=False)
 
     for _ in range(args.warmup):
         step()
@@ -210,6 +226,7 @@ def run_ours(args):
     e1.record(stream)
     e1.synchronize()
     gemm_ms, gemm_flops, gemm_launches = rrf.gemm_profile_end()
+    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
     launches = rrf.launch_count() - l0
     clocks = sampler.stop()
     torch.cuda.synchronize()
@@ -230,11 +247,37 @@ def run_ours(args):
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        getattr(rrf, name)(A, b, q, seed=17, out=outs[name], ws=wss[name], check_status=False)
+        getattr(rrf, name)(A, b, q, seed=17, opts=opts, out=outs[name], ws=wss[name], check_status=False)
         a1.record(stream)
         a1.synchronize()
         t = a0.elapsed_time(a1)
         per[name] = {"ms": round(t, 1), "tflops": round(f / t / 1e9, 4), "gflop": round(f / 1e9, 1)}
+
+    # The plain FP64 method (every product on the DFMA pipe) on the same GPU, one run per method.
+    plain = None
+    if not args.no_plain and args.gemm != "native":
+        popts = rrf.make_opts(gemm_mode=rrf.GEMM_NATIVE)
+        pms = 0.0
+        pper = {}
+        for name in methods:
+            pws = rrf.workspace((rrf.randutv_workspace_bytes if name == "randutv" else rrf.powerurv_workspace_bytes)(
+                n, n, b, popts), dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            getattr(rrf, name)(A, b, q, seed=17, opts=popts, out=outs[name], ws=pws, check_status=False)
+            a1.record(stream)
+            a1.synchronize()
+            t = a0.elapsed_time(a1)
+            pper[name] = round(t, 1)
+            pms += t
+            del pws
+        plain = {"gemm": "native (DFMA)", "ms_per_step": round(pms, 1), "value": round(len(methods) / (pms / 1e3), 5),
+                 "per_method_ms": pper, "speedup_of_value": round((len(methods) / (ms / 1e3)) / (len(methods) / (pms / 1e3)), 3)}
+        # restore the default path's outputs for the accuracy check below
+        for name in methods:
+            getattr(rrf, name)(A, b, q, seed=17, opts=opts, out=outs[name], ws=wss[name], check_status=False)
+        torch.cuda.synchronize()
 
     # End to end through the host-buffer C ABI entry points (pinned host memory, copies timed).
     e2e = None
@@ -244,12 +287,12 @@ def run_ours(args):
         Ah = pinned(n, n)
         Ah[...] = A.cpu().numpy()
         hout = {name: (pinned(n, n), pinned(n, n), pinned(n, n)) for name in ("randutv", "powerurv")}
-        rrf.randutv_host(Ah, b, q, 17, out=hout["randutv"])   # warm-up of the allocator path
+        rrf.randutv_host(Ah, b, q, 17, opts=opts, out=hout["randutv"])   # warm-up of the allocator path
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            rrf.randutv_host(Ah, b, q, 17, out=hout["randutv"])
-            rrf.powerurv_host(Ah, b, q, 17, out=hout["powerurv"])
+            rrf.randutv_host(Ah, b, q, 17, opts=opts, out=hout["randutv"])
+            rrf.powerurv_host(Ah, b, q, 17, opts=opts, out=hout["powerurv"])
         e2e_s = (time.perf_counter() - t0) / args.steps
         if world > 1:
             t = torch.tensor([e2e_s], device=dev)
@@ -277,13 +320,35 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample(np.asfortranarray(A.cpu().numpy()), n, b, q, args.cpu_sample_steps)
 
-    gemm_avg_ms = gemm_ms / max(gemm_launches, 1)
-    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+    peaks, peak_src = measured_peaks()
+    if emu_ms > gemm_ms:
+        # dominant kernel: the emulated GEMM's tensor-core kernel (BF16 digit products, timed inside a long
+        # step -> the sustained BF16 peak)
+        achieved = emu_tflops / (emu_ms / 1e3) / 1e12
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"kernel": "ozaki_gemm_kernel (FP64 product emulated with 7 BF16 digit slices)", "bound": "tensor",
+                "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
+                "work": "28 digit-pair products x 2 M N K' BF16 flops per launch (K' = K rounded up to 32)",
+                "fp64_equivalent_tflops": round(emu_flops / (emu_ms / 1e3) / 1e12, 3),
+                "launches": int(emu_launches), "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),
+                "share_of_step": round(emu_ms / (ms * args.steps), 4),
+                "dfma_gemm": {"ms": round(gemm_ms, 1), "launches": int(gemm_launches),
+                              "tflops": round(gemm_flops / (gemm_ms / 1e3) / 1e12, 4) if gemm_ms > 0 else 0.0}}
+    else:
+        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+        roof = {"kernel": "gemm_f64_kernel (+ split-K reduction)", "bound": "alu", "achieved": round(achieved, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": None,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; recipe nominal 1.25)",
+                "launches": int(gemm_launches), "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4),
+                "share_of_step": round(gemm_ms / (ms * args.steps), 4)}
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "factorizations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": methods,
+        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": methods, "gemm": args.gemm,
                    "seeds": {"Q1": 11, "Q2": 12, "G": 17}, "l2": "inputs larger than L2 (A is 512 MB)",
                    "parallelism": f"replicas x{world}"},
         "tflops": round(world * flops / (ms / 1e3) / 1e12, 4),
@@ -292,12 +357,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": round(launches / args.steps, 1),
-        "roofline": {"kernel": "gemm_f64_kernel (+ split-K reduction)", "bound": "alu", "achieved": round(achieved, 4),
-                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                     "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; recipe nominal 1.25)",
-                     "launches": int(gemm_launches), "avg_launch_ms": round(gemm_avg_ms, 4),
-                     "share_of_step": round(gemm_ms / (ms * args.steps), 4)},
+        "roofline": roof,
+        "plain_fp64": plain,
         "accuracy": accuracy,
         "cpu_baseline": cpu,
     }
@@ -351,10 +412,167 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------ the other configurations --
+def _setup_single_gpu(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    return torch, torch.device("cuda", 0)
+
+
+def _timed(torch, fn, reps):
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _boundary_ratios(torch, T, s, b, ks):
+    return {str(k): round(power_norm(torch, T[k:, k:]) / float(s[k]), 5) for k in ks}
+
+
+def run_c3_c5(args):
+    """c3: randUTV 16384^2, s_j = 1/(1+j), b = 256, q = 2 with the sketch products in BF16 (FP32 accumulate;
+    panel QR, Jacobi and WY updates FP64) against the plain FP64 method on the same GPU; e_k / sigma_{k+1} of
+    both at sampled boundaries.  c5: randUTV 8192^2 (the 8192^2 spectrum), b = 128, learned per-step q with the
+    BF16 sketch against plain FP64 with fixed q = 2; e_k <= 1.1 sigma_{k+1} checked at every boundary."""
+    torch, dev = _setup_single_gpu(args)
+    from paper_2106_13402_gb300 import qpolicy, rrf, testmats
+    c3 = args.workload == "c3"
+    n, b = (16384, 256) if c3 else (8192, 128)
+    q = 2
+    A, s = testmats.make_matrix(n, n, "poly" if c3 else "c2", 21 if c3 else 11, 22 if c3 else 12, device=str(dev))
+    steps = n // b
+    params = None if c3 else qpolicy.load(str(dev))
+    if not c3 and params is None:
+        print(json.dumps({"workload": "c5", "unavailable": "no trained policy packaged"}))
+        return
+    fast = rrf.make_opts(sketch_prec=rrf.SKETCH_BF16, q_policy=rrf.Q_FIXED if c3 else rrf.Q_LEARNED,
+                         mlp_params=params, steps=0 if c3 else steps)
+    plain = rrf.make_opts(gemm_mode=rrf.GEMM_NATIVE)
+    out = (rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev))
+    ws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, fast), dev)
+    for _ in range(args.warmup):
+        rrf.randutv(A, b, q, 17, opts=fast, ws=ws, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = rrf.launch_count()
+    rrf.gemm_profile_begin(200000)
+    ms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=fast, ws=ws, out=out, check_status=False), args.steps)
+    rrf.gemm_profile_end()
+    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    launches = rrf.launch_count() - l0
+    clocks = sampler.stop()
+    st = rrf.lib().rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None))
+    qs = rrf.opts_q_used(fast)[: steps - 1] if not c3 else [q] * (steps - 1)
+    U, T, V = out
+    res = float(torch.linalg.norm(A - U @ T @ V.t()) / torch.linalg.norm(A))
+    ks = list(range(b, n, b)) if not c3 else [b, 16 * b, n // 2, n - 2 * b]
+    r_fast = _boundary_ratios(torch, T, s, b, ks)
+    del ws
+    # plain FP64 (DFMA products, FP64 sketch, fixed q = 2): one timed run
+    pws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, plain), dev)
+    rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out)
+    pms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out, check_status=False), 1)
+    r_plain = _boundary_ratios(torch, out[1], s, b, ks)
+    del pws
+    flops = testmats.flops_randutv(n, n, b, q)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["bf16_tflops_sustained"])
+    ach = emu_tflops / (emu_ms / 1e3) / 1e12 if emu_ms > 0 else 0.0
+    on_target = lambda r: sum(1 for v in r.values() if v <= 1.1)
+    line = {
+        "metric": ("factorizations/s (randUTV, BF16 sketch, 16384^2, b=256, q=2) vs plain FP64" if c3 else
+                   "factorizations/s (randUTV, learned q + BF16 sketch, 8192^2, b=128) vs plain FP64 q=2"),
+        "value": round(1e3 / ms, 5), "unit": "factorizations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (sketch products bf16 x bf16 -> fp32)", "data": "synthetic",
+        "config": {"workload": ("randUTV 16384x16384 A = Q1 diag(1/(1+j)) Q2^T, BF16 sketch" if c3 else
+                                "randUTV 8192x8192 A = Q1 diag(s) Q2^T (s_j = 10^(-8j/n), j < n/2, then 1e-4), "
+                                "learned q + BF16 sketch"), "m": n, "n": n, "b": b, "q": q,
+                   "l2": "inputs larger than L2"},
+        "tflops_model": round(flops / (ms / 1e3) / 1e12, 3),
+        "plain_fp64": {"ms": round(pms, 1), "value": round(1e3 / pms, 5), "speedup": round(pms / ms, 3),
+                       "e_k_over_sigma_k+1": r_plain if c3 else None, "on_target": on_target(r_plain)},
+        "e_k_over_sigma_k+1": r_fast if c3 else None,
+        "on_target": on_target(r_fast), "boundaries": len(ks),
+        "worst_ratio_fast_over_plain": round(max(r_fast[k] / r_plain[k] for k in r_fast), 4),
+        "q_used": None if c3 else {"mean": round(sum(qs) / len(qs), 3), "hist": [qs.count(v) for v in range(4)]},
+        "residual": res, "device_status": int(st), "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_src} bf16_tflops_sustained", "share_of_step": round(emu_ms / (ms * args.steps), 4),
+                     "launches": int(emu_launches)},
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_c4(args):
+    """512 FP32 powerURV factorizations (q = 1) of uneven shape, m ~ U[256, 2048], n ~ U[128, m], mixed decays,
+    in one CUDA graph of persistent batched kernels with autotuned tiles."""
+    torch, dev = _setup_single_gpu(args)
+    from paper_2106_13402_gb300 import rrf, testmats
+    shapes = testmats.batch_shapes(512, 31)
+    plan = rrf.BatchPlan(shapes, b=64, q=1)
+    ws = rrf.workspace(plan.workspace_bytes(), dev)
+    profs = ("exp8", "poly", "step")
+    As = [rrf.as_fortran(testmats.make_matrix(m, n, profs[i % 3], 10000 + i, 20000 + i, device=str(dev))[0].float())
+          for i, (m, n) in enumerate(shapes)]
+    out = plan.allocate(str(dev))
+    t0 = time.perf_counter()
+    plan.run(As, out, 31, ws)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        plan.run(As, out, 31, ws)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = rrf.launch_count()
+    ms = _timed(torch, lambda: plan.run(As, out, 31, ws), args.steps)
+    launches = rrf.launch_count() - l0
+    clocks = sampler.stop()
+    fl = sum(testmats.flops_powerurv(m, n, 1) for m, n in shapes)
+    worst = 0.0
+    for i in range(0, 512, 37):
+        U, T, V = out[0][i], out[1][i], out[2][i]
+        A = As[i]
+        worst = max(worst, float(torch.linalg.norm(A - U @ T @ V.t()) / torch.linalg.norm(A)))
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    line = {
+        "metric": "factorizations/s (512 uneven FP32 powerURV q=1, one CUDA graph)", "value": round(512 / (ms / 1e3), 2),
+        "unit": "factorizations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch of 512: m ~ U[256, 2048], n ~ U[128, m] (seed 31), exp/poly/step decays", "b": 64,
+                   "q": 1, "tiles": list(plan.tiles()), "l2": "inputs 1.5 GB, larger than L2"},
+        "tflops_model": round(fl / (ms / 1e3) / 1e12, 3), "first_run_s_autotune_capture": round(first_s, 2),
+        "worst_sampled_residual": worst, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": {"kernel": "batched FP32 step (whole graph)", "bound": "alu",
+                     "achieved": round(fl / (ms / 1e3) / 1e12, 3), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                     "frac": round(fl / (ms / 1e3) / 1e12 / fp32_peak, 4), "traffic": None,
+                     "peak_source": "152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"},
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("c3", "c5"):
+        run_c3_c5(args)
+    elif args.workload == "c4":
+        run_c4(args)
     else:
         run_ours(args)
 

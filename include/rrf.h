@@ -262,13 +262,17 @@ RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
  * rrf_launch_count: number of GPU kernels this library has launched in this process so far.
  * rrf_gemm_profile_begin: from now on, bracket every FP64 GEMM launch (including its split-K
  *   reduction) with CUDA events on its stream, up to max_launches launches; returns 0 on success.
- * rrf_gemm_profile_end: stop, wait for the recorded events and return the summed GEMM device time
- *   (ms), the algorithmic flops of those launches (sum of 2 M N K over their problems) and the
+ * rrf_gemm_profile_end: stop, wait for the recorded events and return the summed DFMA GEMM device
+ *   time (ms), the algorithmic flops of those launches (sum of 2 M N K over their problems) and the
  *   number of launches timed.  Returns 0 on success.
+ * rrf_gemm_profile_emulated (after rrf_gemm_profile_end): the same for the tensor-core kernel of the
+ *   emulated GEMM (its digit splitting and split-K reduction launches are not included): device time,
+ *   FP64-equivalent flops 2 M N K, tensor flops 28 x 2 M N K' (K' = K rounded up to 32) and launches.
  * ---------------------------------------------------------------------------------------------- */
 RRF_API int64_t rrf_launch_count(void);
 RRF_API int rrf_gemm_profile_begin(int max_launches);
 RRF_API int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches);
+RRF_API int rrf_gemm_profile_emulated(double* ms, double* flops, double* tensor_flops, int64_t* launches);
 
 /* Human-readable name of a status code (static storage). */
 RRF_API const char* rrf_status_string(rrf_status s);

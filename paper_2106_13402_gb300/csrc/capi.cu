@@ -173,7 +173,9 @@ extern "C" rrf_status rrf_panel_qr(int64_t r, int64_t w, double* P, int64_t ldp,
   return RRF_OK;
 }
 
-extern "C" size_t rrf_jacobi_svd_workspace(int64_t) { return kHeaderBytes; }
+extern "C" size_t rrf_jacobi_svd_workspace(int64_t c) {
+  return kHeaderBytes + (c >= 1 && c <= 256 ? jacobi_scratch_bytes(c) : 0);
+}
 
 extern "C" rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                                      double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream) {
@@ -194,7 +196,9 @@ extern "C" rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, do
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(workspace);
   RRF_CUDA_TRY(cudaMemsetAsync(hdr, 0, kHeaderBytes, st));
-  RRF_CUDA_TRY(jacobi_svd(c, M, ldm, Us, ldu, s, Vs, ldv, hdr, st));
+  RRF_CUDA_TRY(jacobi_svd(c, M, ldm, Us, ldu, s, Vs, ldv, hdr, st,
+                          reinterpret_cast<double*>(reinterpret_cast<char*>(workspace) + kHeaderBytes),
+                          ws_bytes - kHeaderBytes));
   return RRF_OK;
 }
 

@@ -167,13 +167,17 @@ int plan_splits(const GemmDesc& d, int sms) {
 }
 
 // Optional instrumentation: CUDA events around each launch (diagnostics API of rrf.h).
+// Event pairs around GEMM launches while profiling is on; kind 0 = DFMA GEMM (kernel + split-K reduce),
+// kind 1 = the emulated GEMM's tensor-core kernel.
 struct GemmProfile {
   std::mutex mu;
   bool on = false;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  std::vector<double> flops, tflops;
   size_t used = 0;
-  double flops = 0.0;
-  int64_t launches = 0;
+  double ms_k[2] = {0.0, 0.0}, flops_k[2] = {0.0, 0.0}, tflops_k[2] = {0.0, 0.0};
+  int64_t launches_k[2] = {0, 0};
 };
 GemmProfile& prof() {
   static GemmProfile p;
@@ -181,6 +185,21 @@ GemmProfile& prof() {
 }
 
 }  // namespace
+
+cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream) {
+  GemmProfile& pf = prof();
+  if (!pf.on) return nullptr;
+  std::lock_guard<std::mutex> lock(pf.mu);
+  if (!pf.on || pf.used + 2 > pf.ev.size()) return nullptr;
+  cudaEventRecord(pf.ev[pf.used], stream);
+  const size_t r = pf.used / 2;
+  pf.kind[r] = kind;
+  pf.flops[r] = flops;
+  pf.tflops[r] = tensor_flops;
+  cudaEvent_t end = pf.ev[pf.used + 1];
+  pf.used += 2;
+  return end;
+}
 
 size_t gemm_scratch_bytes(const GemmDesc* d, int count) {
   const int sms = dev_info().sms;
@@ -234,18 +253,9 @@ cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scrat
   if (batch.count == 0) return cudaSuccess;
   batch.total_units = units;
   batch.total_elems = elems;
-  GemmProfile& pf = prof();
-  cudaEvent_t ev_end = nullptr;
-  if (pf.on) {
-    std::lock_guard<std::mutex> lock(pf.mu);
-    if (pf.used + 2 <= pf.ev.size()) {
-      cudaEventRecord(pf.ev[pf.used], stream);
-      ev_end = pf.ev[pf.used + 1];
-      pf.used += 2;
-      for (int i = 0; i < batch.count; ++i) pf.flops += 2.0 * batch.p[i].d.M * batch.p[i].d.N * batch.p[i].d.K;
-      pf.launches += 1;
-    }
-  }
+  double fl = 0.0;
+  for (int i = 0; i < batch.count; ++i) fl += 2.0 * batch.p[i].d.M * batch.p[i].d.N * batch.p[i].d.K;
+  cudaEvent_t ev_end = profile_launch_begin(0, fl, 0.0, stream);
   gemm_f64_kernel<<<(unsigned)units, NT, 0, stream>>>(batch);
   count_launch();
   cudaError_t e = cudaGetLastError();
@@ -272,9 +282,14 @@ extern "C" int rrf_gemm_profile_begin(int max_launches) {
     if (cudaEventCreate(&e) != cudaSuccess) return 1;
     pf.ev.push_back(e);
   }
+  pf.kind.assign(pf.ev.size() / 2, 0);
+  pf.flops.assign(pf.ev.size() / 2, 0.0);
+  pf.tflops.assign(pf.ev.size() / 2, 0.0);
   pf.used = 0;
-  pf.flops = 0.0;
-  pf.launches = 0;
+  for (int k = 0; k < 2; ++k) {
+    pf.ms_k[k] = pf.flops_k[k] = pf.tflops_k[k] = 0.0;
+    pf.launches_k[k] = 0;
+  }
   pf.on = true;
   return 0;
 }
@@ -282,16 +297,32 @@ extern "C" int rrf_gemm_profile_begin(int max_launches) {
 extern "C" int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches) {
   rrf::GemmProfile& pf = rrf::prof();
   std::lock_guard<std::mutex> lock(pf.mu);
-  pf.on = false;
-  double total = 0.0;
-  for (size_t i = 0; i + 1 < pf.used; i += 2) {
-    if (cudaEventSynchronize(pf.ev[i + 1]) != cudaSuccess) return 1;
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]) != cudaSuccess) return 1;
-    total += t;
+  if (pf.on) {
+    pf.on = false;
+    for (size_t i = 0; i + 1 < pf.used; i += 2) {
+      if (cudaEventSynchronize(pf.ev[i + 1]) != cudaSuccess) return 1;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]) != cudaSuccess) return 1;
+      const int k = pf.kind[i / 2];
+      pf.ms_k[k] += t;
+      pf.flops_k[k] += pf.flops[i / 2];
+      pf.tflops_k[k] += pf.tflops[i / 2];
+      pf.launches_k[k] += 1;
+    }
   }
-  if (ms) *ms = total;
-  if (flops) *flops = pf.flops;
-  if (launches) *launches = pf.launches;
+  if (ms) *ms = pf.ms_k[0];
+  if (flops) *flops = pf.flops_k[0];
+  if (launches) *launches = pf.launches_k[0];
+  return 0;
+}
+
+extern "C" int rrf_gemm_profile_emulated(double* ms, double* flops, double* tensor_flops, int64_t* launches) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  if (pf.on) return 1;
+  if (ms) *ms = pf.ms_k[1];
+  if (flops) *flops = pf.flops_k[1];
+  if (tensor_flops) *tensor_flops = pf.tflops_k[1];
+  if (launches) *launches = pf.launches_k[1];
   return 0;
 }

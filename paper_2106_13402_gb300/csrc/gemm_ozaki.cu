@@ -17,10 +17,10 @@
 // 7..12 are dropped (at most 2^-51.4 max|a_r.| max|b_.c| per k, ~2^-56 for random digits).  At the end
 // C = alpha 2^(e_r + f_c - 48) (acc + frac) + beta C in FP64.
 //
-// Kernel (320 threads, persistent over 128 x 32 output tiles x K splits): warp 0 lane 0 loads the 7 + 7
+// Kernel (576 threads, persistent over 128 x 32 output tiles x K splits): warp 0 lane 0 loads the 7 + 7
 // digit tiles of each 32-wide K chunk with TMA (64-byte swizzle, 3-stage ring); warp 1 lane 0 issues, per
 // 16-wide K step and A digit a, one MMA of A_a against the B digits 0..6-a laid back to back (N = (7-a) 32),
-// into two TMEM accumulator buffers of 7 x 32 columns used alternately; warps 2..9 read a buffer
+// into two TMEM accumulator buffers of 7 x 32 columns used alternately; warps 2..17 read a buffer
 // (tcgen05.ld) while the MMAs fill the other.  All mbarrier waits are bounded (RRF_TIMEOUT, drain, free
 // TMEM, exit).
 #include <cuda.h>
@@ -38,8 +38,8 @@ constexpr int kS = 7;            // digits per value
 constexpr int BM = 128, BN = 32;
 constexpr int KC = 32;           // K per chunk / stage (64 bytes of BF16: 64-byte swizzle)
 constexpr int kStages = 3;
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kBufCols = 256;    // TMEM columns between the two accumulator buffers (7 x BN = 224 used)
 constexpr int kGroupM = 8;       // tile raster: groups of 8 row tiles, column tiles fastest inside a group
 constexpr int64_t kMaxSplitK = 65536;  // K of one split: keeps the int64 accumulator below 2^63
@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (g > 0) mbar_wait(&acc_full[(g - 1) & 1], (uint32_t)((g - 1) >> 1) & 1);
     }
   } else {
-    // Epilogue warps ew = 0..7: TMEM lane quadrant (warp % 4) = 32 tile rows, columns 16 (ew / 4) .. +15.
+    // Epilogue warps ew = 0..15: TMEM lane quadrant (warp % 4) = 32 tile rows, columns 8 (ew / 4) .. +7.
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int col0 = (ew >> 2) * 16;
+    const int col0 = (ew >> 2) * 8;
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
     int64_t g = 0;
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
@@ -275,10 +275,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nch = unit_chunks(p, split, k0);
       // acc: sum over chunks of S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 (exact); ta: the rest,
       // S_5 2^-8 + S_6 2^-16, in the same unit, with its integer part moved into acc after every chunk.
-      long long acc[16];
-      float ta[16];
+      long long acc[8];
+      float ta[8];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) { acc[c] = 0; ta[c] = 0.f; }
+      for (int c = 0; c < 8; ++c) { acc[c] = 0; ta[c] = 0.f; }
       bool ok = true;
       for (int i = 0; i < nch; ++i, ++g) {
         const int bf = (int)(g & 1);
@@ -289,35 +289,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t v[kS][8];
 #pragma unroll
-        for (int h = 0; h < 16; h += 8) {
-          uint32_t v[kS][8];
-#pragma unroll
-          for (int d = 0; d < kS; ++d) tmem_ld8(trow + (uint32_t)(bf * kBufCols + d * BN + h), v[d]);
-          tmem_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            // |S_d| <= (d + 1) 32 2^14 <= 2^22 for every diagonal: each converts exactly.
-            const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^28
-            const int mid = exact_int(v[2][c]) * 256 + exact_int(v[3][c]);  // |.| < 2^30
-            float t = fmaf(__uint_as_float(v[5][c]), 0.00390625f, ta[h + c]);
-            t = fmaf(__uint_as_float(v[6][c]), 1.52587890625e-05f, t);
-            const float r = __fadd_rn(t, kMagic);
-            const int ti = __float_as_int(r) - kMagicBits;
-            ta[h + c] = __fsub_rn(t, __fsub_rn(r, kMagic));
-            acc[h + c] += (long long)hi * 16777216LL + (long long)mid * 256LL + (long long)(exact_int(v[4][c]) + ti);
-          }
-        }
+        for (int d = 0; d < kS; ++d) tmem_ld8(trow + (uint32_t)(bf * kBufCols + d * BN), v[d]);
+        tmem_wait_ld();
+        // the buffer may be refilled as soon as every warp holds its values
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[bf]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          // |S_d| <= (d + 1) 32 2^14 <= 2^22 for every diagonal: each converts exactly.
+          const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^28
+          const int mid = exact_int(v[2][c]) * 256 + exact_int(v[3][c]);  // |.| < 2^30
+          float t = fmaf(__uint_as_float(v[5][c]), 0.00390625f, ta[c]);
+          t = fmaf(__uint_as_float(v[6][c]), 1.52587890625e-05f, t);
+          const float r = __fadd_rn(t, kMagic);
+          const int ti = __float_as_int(r) - kMagicBits;
+          ta[c] = __fsub_rn(t, __fsub_rn(r, kMagic));
+          acc[c] += (long long)hi * 16777216LL + (long long)mid * 256LL + (long long)(exact_int(v[4][c]) + ti);
+        }
       }
       if (!ok || *(volatile int*)&abort_flag) break;
       const int64_t row = m0 + quad * 32 + lane;
       if (row >= p.M) continue;
       const int er = p.ea[row];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
         const int64_t col = n0 + col0 + c;
         if (col >= p.N) continue;
         // value = 2^(e_r + f_c) sum_d S_d 2^-8(d+2) = (acc + ta) 2^(e_r + f_c - 48)
@@ -554,8 +552,11 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   p.ct = out_transposed ? 1 : 0;
   p.status = status;
   const unsigned grid = (unsigned)std::min<int64_t>(p.units, sms);
+  // profiled work: the FP64 product's 2 M N K, and the tensor work 28 x 2 M N Kp of the digit products
+  cudaEvent_t ev_end = profile_launch_begin(1, 2.0 * M * N * K, 56.0 * M * N * Kp, s);
   ozaki_gemm_kernel<<<grid, kThreads, oz_smem(), s>>>(ma, mb, p);
   count_launch();
+  if (ev_end != nullptr) cudaEventRecord(ev_end, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const int64_t blocks = std::min<int64_t>((M * N + 255) / 256, (int64_t)sms * 16);

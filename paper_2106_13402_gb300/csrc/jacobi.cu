@@ -39,6 +39,8 @@ struct JacobiArgs {
   double* s;
   double* Vs;
   int64_t ldv;
+  const double* V0;  // optional starting V (c x c, orthogonal); null = identity
+  int64_t ldv0;
   WsHeader* hdr;
 };
 
@@ -76,12 +78,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
   const int tid = threadIdx.x;
   const int r0 = rank * rp;
   const int nloc = max(0, min(rp, c - r0));
-  // Load my rows of M; V starts as the identity.
+  // Load my rows of M; V starts as V0 (or the identity).
   for (int idx = tid; idx < c * rp; idx += NT) {
     const int col = idx / rp, i = idx % rp;
     const int gi = r0 + i;
     Ml[col * ldl + i] = (i < nloc) ? a.M[gi + (int64_t)col * a.ldm] : 0.0;
-    Vl[col * ldl + i] = (i < nloc && gi == col) ? 1.0 : 0.0;
+    if (a.V0 != nullptr)
+      Vl[col * ldl + i] = (i < nloc) ? a.V0[gi + (int64_t)col * a.ldv0] : 0.0;
+    else
+      Vl[col * ldl + i] = (i < nloc && gi == col) ? 1.0 : 0.0;
   }
   if (tid == 0) s_rot = 0;
   cluster.sync();
@@ -250,6 +255,92 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
   cluster.sync();  // keep shared memory alive until every CTA is done reading it
 }
 
+// FP32 pre-pass (c <= 128, one CTA): Hestenes sweeps on R 2^-e (scaled into FP32 range) in shared memory,
+// one warp per column pair, until a sweep without rotations at tolerance 2^-16 or kPreSweeps sweeps (the
+// FP64 sweeps converge quadratically from there: 2^-16 -> 2^-32 -> below c 2^-53).  Only the
+// accumulated rotation V32 leaves the kernel: it is a preconditioner, orthonormalized in FP64 afterwards,
+// and the FP64 sweeps that follow decide the result.
+constexpr int kPreThreads = 1024;
+constexpr int kPreMinC = 32;
+constexpr int kPreMaxC = 128;
+constexpr int kPreSweeps = 10;
+
+__global__ void __launch_bounds__(kPreThreads, 1)
+    jacobi_f32_prepass_kernel(int c, const double* __restrict__ M, int64_t ldm, double* __restrict__ Vout,
+                              int64_t ldvo) {
+  extern __shared__ float sm32[];
+  float* Ms = sm32;          // [c][c], column k at k * c
+  float* Vs = sm32 + c * c;  // [c][c]
+  __shared__ double s_part[kPreThreads / 32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double mx = 0.0;
+  for (int idx = tid; idx < c * c; idx += kPreThreads) mx = fmax(mx, fabs(M[(idx % c) + (int64_t)(idx / c) * ldm]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_part[warp] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < kPreThreads / 32; ++w) mx = fmax(mx, s_part[w]);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  for (int idx = tid; idx < c * c; idx += kPreThreads) {
+    const int i = idx % c, k = idx / c;
+    Ms[idx] = (float)ldexp(M[i + (int64_t)k * ldm], -ex);
+    Vs[idx] = (i == k) ? 1.f : 0.f;
+  }
+  if (tid == 0) s_rot = 0;
+  __syncthreads();
+  const int ne = c + (c & 1), npairs = ne / 2, rounds = ne - 1;
+  const float tol = 0x1p-16f;
+  for (int sweep = 0; sweep < kPreSweeps; ++sweep) {
+    for (int t = 0; t < rounds; ++t) {
+      for (int g = warp; g < npairs; g += kPreThreads / 32) {
+        int p, q;
+        round_pair(t, g, ne, p, q);
+        if (q >= c) continue;
+        float* mp = Ms + p * c;
+        float* mq = Ms + q * c;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < c; i += 32) {
+          const float x = mp[i], y = mq[i];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = 1.f / sqrtf(1.f + tt * tt);
+          const float sn = cs * tt;
+          float* vp = Vs + p * c;
+          float* vq = Vs + q * c;
+          for (int i = lane; i < c; i += 32) {
+            const float x = mp[i], y = mq[i];
+            mp[i] = cs * x - sn * y;
+            mq[i] = sn * x + cs * y;
+            const float u = vp[i], v = vq[i];
+            vp[i] = cs * u - sn * v;
+            vq[i] = sn * u + cs * v;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const bool done = (s_rot == 0);
+    __syncthreads();
+    if (done) break;
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+  }
+  for (int idx = tid; idx < c * c; idx += kPreThreads) Vout[(idx % c) + (int64_t)(idx / c) * ldvo] = (double)Vs[idx];
+}
+
 // Gram-Schmidt completion of u_k for exactly-zero singular values (two passes against the columns
 // already present, candidates e_0, e_1, ... in order).  Runs only when the Jacobi kernel flagged it.
 __global__ void __launch_bounds__(NT) complete_kernel(int c, double* Us, int64_t ldu, const double* s,
@@ -314,8 +405,16 @@ size_t jacobi_smem(int c) {
 
 }  // namespace
 
+size_t jacobi_scratch_bytes(int64_t c) {
+  if (c < kPreMinC || c > kPreMaxC) return 0;
+  GemmDesc g;
+  g.M = c; g.N = c; g.K = c;
+  return align_up((size_t)3 * c * c * sizeof(double), 256) + gemm_scratch_bytes(&g, 1);
+}
+
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
-                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream) {
+                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch,
+                       size_t scratch_bytes) {
   if (c <= 0) return cudaSuccess;
   if (c > kMaxC) return cudaErrorInvalidValue;
   JacobiArgs a;
@@ -328,14 +427,68 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   a.s = s;
   a.Vs = Vs;
   a.ldv = ldv;
+  a.V0 = nullptr;
+  a.ldv0 = 0;
   a.hdr = hdr;
+  cudaError_t e;
+  const size_t need = jacobi_scratch_bytes(c);
+  if (scratch != nullptr && need > 0 && scratch_bytes >= need) {
+    // Mixed precision: FP32 sweeps give V32; two Newton-Schulz steps X <- X + X (I - X^T X) / 2 make it
+    // orthogonal to FP64 accuracy (the error squares each step); the FP64 sweeps then start from
+    // M V0, whose columns are already nearly orthogonal, with V accumulated onto V0.
+    double* X = scratch;
+    double* Y = scratch + c * c;
+    double* E = scratch + 2 * c * c;
+    double* gs = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) +
+                                           align_up((size_t)3 * c * c * sizeof(double), 256));
+    const size_t gs_bytes = scratch_bytes - align_up((size_t)3 * c * c * sizeof(double), 256);
+    static bool attr_pre = false;
+    if (!attr_pre) {
+      e = cudaFuncSetAttribute(jacobi_f32_prepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(2 * kPreMaxC * kPreMaxC * sizeof(float)));
+      if (e != cudaSuccess) return e;
+      attr_pre = true;
+    }
+    jacobi_f32_prepass_kernel<<<1, kPreThreads, 2 * c * c * sizeof(float), stream>>>((int)c, M, ldm, X, c);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int it = 0; it < 2; ++it) {
+      if ((e = fill_identity(c, c, E, c, stream)) != cudaSuccess) return e;
+      GemmDesc g1;  // E = I - X^T X
+      g1.M = c; g1.N = c; g1.K = c;
+      g1.A = X; g1.lda = c; g1.ta = 1;
+      g1.B = X; g1.ldb = c; g1.tb = 0;
+      g1.C = E; g1.ldc = c;
+      g1.alpha = -1.0; g1.beta = 1.0;
+      if ((e = gemm_f64(&g1, 1, gs, gs_bytes, stream)) != cudaSuccess) return e;
+      if ((e = copy_matrix(c, c, X, c, Y, c, stream)) != cudaSuccess) return e;
+      GemmDesc g2 = g1;  // Y = X + X E / 2
+      g2.A = X; g2.ta = 0;
+      g2.B = E; g2.tb = 0;
+      g2.C = Y;
+      g2.alpha = 0.5; g2.beta = 1.0;
+      if ((e = gemm_f64(&g2, 1, gs, gs_bytes, stream)) != cudaSuccess) return e;
+      std::swap(X, Y);
+    }
+    GemmDesc g3;  // Y = M V0
+    g3.M = c; g3.N = c; g3.K = c;
+    g3.A = M; g3.lda = ldm; g3.ta = 0;
+    g3.B = X; g3.ldb = c; g3.tb = 0;
+    g3.C = Y; g3.ldc = c;
+    g3.alpha = 1.0; g3.beta = 0.0;
+    if ((e = gemm_f64(&g3, 1, gs, gs_bytes, stream)) != cudaSuccess) return e;
+    a.M = Y;
+    a.ldm = c;
+    a.V0 = X;
+    a.ldv0 = c;
+  }
   const size_t smem = jacobi_smem((int)c);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxC));
     attr = true;
   }
-  cudaError_t e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
+  e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   jacobi_kernel<<<CL, NT, smem, stream>>>(a);
   count_launch();

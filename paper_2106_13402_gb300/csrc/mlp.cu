@@ -6,13 +6,18 @@
 // W3 (4 x 64), b3 (4)] = 5508 values.  Training keeps an FP32 master copy plus Adam moments.
 //
 // Features of step i (from the q = 0 sketch Y0 = T22^T G and the R factor of its Householder QR, whose
-// diagonal magnitudes rank the sampled directions like singular values):
+// diagonal magnitudes |R(j, j)| approximate the energy of T22 beyond its first j sampled directions, and
+// from the singular values D of the previous step's b x b core, the exact spectrum just before the block):
 //   f0..f7 = log10(|R(k_j, k_j)| / |R(0, 0)|), k_j = (j + 1) b / 8 - 1       (decay inside the block)
 //   f8 = (i - 1) / steps, f9 = log2(n) / 16, f10 = log2(c) / 16            (where in the factorization)
 //   f11 = log10(|R(b-1, b-1)| / |R(b/2, b/2)|)                              (decay at the block edge)
 //   f12 = mean_k log10(|R(k, k)| / |R(0, 0)|)
-//   f13 = log10(||Y0||_F / (|R(0, 0)| sqrt(b)))
-//   f14 = q chosen for the previous step / 3, f15 = 1.
+//   f13 = log10(|R(0, 0)| / D(b-1))         (energy of T22 against the last singular value before it)
+//   f14 = log10(D(b-1) / D(0))              (decay rate over the previous block)
+//   f15 = log10(|R(b-1, b-1)| / D(b-1))     (energy beyond the block against that singular value)
+// f13..f15 are 0 at step 1 (no previous block); every feature is clamped to [-30, 30].
+// The policy takes the smallest q whose cumulative softmax probability reaches kQConfidence, so an
+// uncertain network errs towards more power iterations.
 #include <algorithm>
 
 #include "rrf_internal.cuh"
@@ -20,6 +25,7 @@
 namespace rrf {
 
 constexpr int kIn = 16, kH = 64, kOut = 4;
+constexpr float kQConfidence = 0.8f;  // cumulative probability the chosen q must reach
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kIn, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kOut * kH, kNumParams = kOffB3 + kOut;
 
@@ -184,45 +190,33 @@ __global__ void adam_kernel(float* __restrict__ master, float* __restrict__ m, f
 }
 
 // Features of one randUTV step (see the file comment) from the panel-factored q = 0 sketch.
-__global__ void features_kernel(const double* __restrict__ Rdiag_src, int64_t ldr, int b, double y0_fro2,
-                                const double* __restrict__ y0fro2_dev, int step, int steps, int64_t n, int64_t c,
-                                int q_prev, float* __restrict__ f) {
+__global__ void features_kernel(const double* __restrict__ Rdiag_src, int64_t ldr, int b,
+                                const double* __restrict__ Dprev, int step, int steps, int64_t n, int64_t c,
+                                float* __restrict__ f) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double fro2 = y0fro2_dev ? *y0fro2_dev : y0_fro2;
   auto d = [&](int k) { return fabs(Rdiag_src[k + (int64_t)k * ldr]) + 1e-300; };
+  auto lg = [](double x) { return (float)fmin(30.0, fmax(-30.0, log10(x))); };
   const double d0 = d(0);
   for (int j = 0; j < 8; ++j) {
     int k = (j + 1) * b / 8 - 1;
     if (k < 0) k = 0;
-    f[j] = (float)log10(d(k) / d0);
+    f[j] = lg(d(k) / d0);
   }
   f[8] = (float)(step - 1) / (float)steps;
   f[9] = (float)(log2((double)n) / 16.0);
   f[10] = (float)(log2((double)c) / 16.0);
-  f[11] = (float)log10(d(b - 1) / d(b / 2));
+  f[11] = lg(d(b - 1) / d(b / 2));
   double mean = 0.0;
   for (int k = 0; k < b; ++k) mean += log10(d(k) / d0);
-  f[12] = (float)(mean / b);
-  f[13] = (float)log10(sqrt(fro2) / (d0 * sqrt((double)b)) + 1e-300);
-  f[14] = (float)q_prev / 3.f;
-  f[15] = 1.f;
-}
-
-// Frobenius norm squared of an r x c block (one CTA, fixed-order reduction).
-__global__ void fro2_kernel(int64_t rows, int64_t cols, const double* __restrict__ X, int64_t ld, double* out) {
-  __shared__ double red[256];
-  double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-    const double v = X[(e % rows) + (e / rows) * ld];
-    acc = fma(v, v, acc);
+  f[12] = (float)fmin(30.0, fmax(-30.0, mean / b));
+  if (Dprev != nullptr) {
+    const double dl = fabs(Dprev[b - 1]) + 1e-300, df = fabs(Dprev[0]) + 1e-300;
+    f[13] = lg(d0 / dl);
+    f[14] = lg(dl / df);
+    f[15] = lg(d(b - 1) / dl);
+  } else {
+    f[13] = f[14] = f[15] = 0.f;
   }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Policy inference for one feature vector: argmax of the logits -> q (device int).
@@ -235,10 +229,17 @@ __global__ void policy_kernel(const __half* __restrict__ params, const float* __
     float x[kIn], z[kOut];
     for (int i = 0; i < kIn; ++i) x[i] = f[i];
     mlp_forward_one(P, x, z, nullptr, nullptr);
-    int best = 0;
-    for (int o = 1; o < kOut; ++o)
-      if (z[o] > z[best]) best = o;
-    *q_out = best;
+    float zmax = z[0];
+    for (int o = 1; o < kOut; ++o) zmax = fmaxf(zmax, z[o]);
+    float e[kOut], tot = 0.f;
+    for (int o = 0; o < kOut; ++o) tot += (e[o] = expf(z[o] - zmax));
+    int pick = kOut - 1;
+    float cum = 0.f;
+    for (int o = 0; o < kOut; ++o) {
+      cum += e[o];
+      if (cum >= kQConfidence * tot) { pick = o; break; }
+    }
+    *q_out = pick;
     if (logits_out)
       for (int o = 0; o < kOut; ++o) logits_out[o] = z[o];
   }
@@ -247,11 +248,9 @@ __global__ void policy_kernel(const __half* __restrict__ params, const float* __
 }  // namespace
 
 // ---- internal entry points used by the randUTV driver --------------------------------------------------
-cudaError_t policy_features(const double* Rfac, int64_t ldr, int b, const double* Y0, int64_t c, double* fro2_scratch,
-                            int step, int steps, int64_t n, int q_prev, float* feat, cudaStream_t s) {
-  fro2_kernel<<<1, 256, 0, s>>>(c, b, Y0, c, fro2_scratch);
-  count_launch();
-  features_kernel<<<1, 32, 0, s>>>(Rfac, ldr, b, 0.0, fro2_scratch, step, steps, n, c, q_prev, feat);
+cudaError_t policy_features(const double* Rfac, int64_t ldr, int b, const double* Dprev, int step, int steps,
+                            int64_t n, int64_t c, float* feat, cudaStream_t s) {
+  features_kernel<<<1, 32, 0, s>>>(Rfac, ldr, b, Dprev, step, steps, n, c, feat);
   count_launch();
   return cudaGetLastError();
 }

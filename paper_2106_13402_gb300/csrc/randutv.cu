@@ -36,10 +36,9 @@ struct RWs {
   int64_t ldtb = 0, ldtbt = 0, ldxh = 0;
   float* part = nullptr;
   size_t part_bytes = 0;
-  // learned q policy: features of the current step, the chosen q, a scratch scalar
+  // learned q policy: features of the current step, the chosen q
   float* feat = nullptr;
   int* qdev = nullptr;
-  double* fro2 = nullptr;
 };
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
@@ -69,7 +68,6 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& 
   w.sig = ar.take<double>(b);
   w.feat = ar.take<float>(16);
   w.qdev = ar.take<int>(4);
-  w.fro2 = ar.take<double>(4);
   w.panel_bytes = panel_scratch_bytes(mx, b);
   w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
   // split-K partials of the DFMA GEMMs; between them it also serves as the small SVD's scratch
@@ -268,7 +266,6 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
 
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
   const bool learned = opts != nullptr && opts->q_policy == RRF_Q_LEARNED;
-  int q_prev = q;
   for (int64_t i = 1; i <= steps; ++i) {
     const int64_t o = b * (i - 1);
     const int64_t r = m - o, c = n - o;
@@ -283,7 +280,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         // Features from the q = 0 sketch (the R of its Householder QR), MLP -> q for this step.
         RRF_CUDA_TRY(copy_matrix(c, b, w.Y, c, w.Qt, c, s));
         RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s));
-        RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, w.Y, c, w.fro2, (int)i, (int)steps, n, q_prev, w.feat, s));
+        RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, i > 1 ? w.sig : nullptr, (int)i, (int)steps, n, c, w.feat, s));
         if (opts->mlp_params != nullptr) {
           RRF_CUDA_TRY(policy_decide(opts->mlp_params, w.feat, w.qdev, s));
           int qh = q;
@@ -304,7 +301,6 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         }
       }
       if (opts != nullptr && opts->q_used_out != nullptr) opts->q_used_out[i - 1] = qi;
-      q_prev = qi;
       RRF_CUDA_TRY(sketch_continue(r, c, b, T22, ldt, qi, bf16, reorth, start, w, s));
       // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
       RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,

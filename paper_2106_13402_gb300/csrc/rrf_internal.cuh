@@ -88,6 +88,10 @@ size_t gemm_scratch_bytes(const GemmDesc* d, int count);
 cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scratch_bytes,
                      cudaStream_t stream);
 
+// While GEMM profiling is on: record a start event on `stream` and return the end event to record after
+// the launch (null when profiling is off or its event pool is used up).  kind 0 = DFMA GEMM, 1 = emulated.
+cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream);
+
 // ---- FP64 GEMM emulated on the BF16 tensor cores (gemm_ozaki.cu) -------------------------------------
 bool ozaki_eligible(const GemmDesc& d, bool force);
 size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K);
@@ -123,9 +127,12 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
                      size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream);
 
 // ---- Jacobi SVD (jacobi.cu) -----------------------------------------------------------------------
-// One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.
+// One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.  With scratch of at least
+// jacobi_scratch_bytes(c) (> 0 for 32 <= c <= 128) an FP32 pre-pass supplies the starting V.
+size_t jacobi_scratch_bytes(int64_t c);
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
-                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream);
+                       double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch = nullptr,
+                       size_t scratch_bytes = 0);
 
 // ---- BF16 tensor-core GEMM (gemm_bf16_tc.cu) ------------------------------------------------------
 // D (FP64, M x N, ldd) = alpha * A (M x K) B (N x K)^T, BF16 operands with K contiguous (ld multiple of 8,
@@ -143,8 +150,9 @@ cudaError_t to_bf16_t(int64_t rows, int64_t cols, const double* S, int64_t lds, 
 
 // ---- learned q policy (mlp.cu) ------------------------------------------------------------------------
 // features of one step from the panel-factored q = 0 sketch (R on and above the diagonal of Rfac, ld ldr)
-cudaError_t policy_features(const double* Rfac, int64_t ldr, int b, const double* Y0, int64_t c, double* fro2_scratch,
-                            int step, int steps, int64_t n, int q_prev, float* feat, cudaStream_t s);
+// and the previous step's singular values Dprev (b of them; null at step 1)
+cudaError_t policy_features(const double* Rfac, int64_t ldr, int b, const double* Dprev, int step, int steps,
+                            int64_t n, int64_t c, float* feat, cudaStream_t s);
 cudaError_t policy_decide(const void* params, const float* feat, int* q_dev, cudaStream_t s);
 
 // ---- small kernels (aux.cu) ------------------------------------------------------------------------

@@ -3,13 +3,13 @@
 Training data comes from the method itself: each training matrix A = Q1 diag(s) Q2^T (seeded Haar factors,
 a random decay class) is factored with q = 0 (recording the 16 features of every step through the C ABI)
 and with fixed q = 1, 2, 3; the judge is the rank-k error e_k = ||T(k:, k:)||_2 at every block boundary
-k (Sec. 4.1) against the quality target e_k <= 1.1 sigma_{k+1}.  A step's label is the cheapest q that
-meets the target there, and the fallback q = 2 where none does, so the policy saves power iterations
-where the local spectrum decays fast and spends one more where q = 2 falls short.  The MLP is trained on
-the GPU with the library's FP16 forward/backward kernels and Adam; without parameters the method falls
-back to q = 2.
+k (Sec. 4.1).  A q is acceptable at a boundary when its e_k meets the quality target 1.1 sigma_{k+1}, or
+else comes within 5 % of the best of q = 2 (the fallback) and q = 3; the label is the cheapest acceptable
+q.  The MLP is trained on the GPU with the library's FP16 forward/backward kernels and Adam; at run time
+the step takes the smallest q whose cumulative softmax probability reaches 0.8.  Without parameters the
+method falls back to q = 2.
 
-    python -m paper_2106_13402_gb300.qpolicy --count 800 --n 1024     # writes qpolicy_fp16.npy
+    python -m paper_2106_13402_gb300.qpolicy --count 1000 --n 1024     # writes qpolicy_fp16.npy
 """
 from __future__ import annotations
 
@@ -80,9 +80,15 @@ def spectral_norm(torch, M, iters: int = 40) -> float:
     return float(math.sqrt(float(s)))
 
 
-def label_matrix(A, s, b: int, seed: int, target: float = 1.1, qmax: int = 3):
-    """Features of each step (q = 0 run), e_k for q = 0..qmax, and labels: the smallest q whose e_k meets
-    target * sigma_{k+1}, or the fallback q = 2 where none does."""
+def acceptable(errs: np.ndarray, sig: np.ndarray, target: float = 1.1, slack: float = 1.05) -> np.ndarray:
+    """errs: (4, k) e_k for q = 0..3; sig: (k,) sigma_{k+1}.  True where q meets target * sigma_{k+1} or
+    comes within `slack` of min(e(q=2), e(q=3))."""
+    ref = np.minimum(errs[2], errs[3])
+    return errs <= np.maximum(target * sig, slack * ref)[None, :]
+
+
+def label_matrix(A, s, b: int, seed: int):
+    """Features of each step (q = 0 run), e_k for q = 0..3, and labels: the cheapest acceptable q."""
     import torch
     n = A.shape[1]
     steps = math.ceil(n / b)
@@ -90,15 +96,22 @@ def label_matrix(A, s, b: int, seed: int, target: float = 1.1, qmax: int = 3):
     opts = rrf.make_opts(q_policy=rrf.Q_LEARNED, steps=steps)
     _, T0, _ = rrf.randutv(A, b, 0, seed, opts=opts, ws=ws)
     feats = rrf.opts_features(opts)[: steps - 1]
-    errs = np.zeros((qmax + 1, steps - 1))
-    for q in range(qmax + 1):
+    errs = np.zeros((4, steps - 1))
+    for q in range(4):
         T = T0 if q == 0 else rrf.randutv(A, b, q, seed, ws=ws)[1]
         for i in range(1, steps):
             errs[q, i - 1] = spectral_norm(torch, T[i * b:, i * b:])
     sig = np.asarray(s)[b * np.arange(1, steps)]
-    ok = errs <= target * sig[None, :]
-    labels = np.array([int(np.argmax(ok[:, i])) if ok[:, i].any() else FALLBACK_Q for i in range(steps - 1)])
+    labels = np.argmax(acceptable(errs, sig), axis=0)
     return feats, labels, errs
+
+
+def decide(logits: np.ndarray, confidence: float = 0.8) -> np.ndarray:
+    """The run-time rule: smallest q whose cumulative softmax probability reaches `confidence`."""
+    z = logits - logits.max(axis=1, keepdims=True)
+    p = np.exp(z)
+    p /= p.sum(axis=1, keepdims=True)
+    return np.argmax(np.cumsum(p, axis=1) >= confidence, axis=1)
 
 
 def generate(count: int, n: int, b: int, seed0: int = 1000, log=None):
@@ -171,7 +184,7 @@ def load(device="cuda", path: str = WEIGHTS):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--count", type=int, default=800)
+    ap.add_argument("--count", type=int, default=1000)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--epochs", type=int, default=100)

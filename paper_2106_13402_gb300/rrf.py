@@ -30,7 +30,7 @@ EXPORTED = [
     "rrf_gemm_bf16_workspace", "rrf_gemm_bf16", "rrf_batch_plan_create", "rrf_batch_plan_workspace",
     "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
     "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
-    "rrf_gemm_emulated",
+    "rrf_gemm_emulated", "rrf_gemm_profile_emulated",
 ]
 
 
@@ -143,6 +143,9 @@ def lib():
             L.rrf_gemm_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_int64)]
             L.rrf_gemm_profile_end.restype = ctypes.c_int
+            L.rrf_gemm_profile_emulated.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [
+                ctypes.POINTER(ctypes.c_int64)]
+            L.rrf_gemm_profile_emulated.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -407,6 +410,15 @@ def gemm_profile_end():
     if lib().rrf_gemm_profile_end(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)) != 0:
         raise RuntimeError("rrf_gemm_profile_end failed")
     return ms.value, fl.value, n.value
+
+
+def gemm_profile_emulated():
+    """After gemm_profile_end: (device ms, FP64-equivalent flops, tensor flops, launches) of the emulated
+    GEMM's tensor-core kernel."""
+    ms, fl, tf, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    if lib().rrf_gemm_profile_emulated(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(tf), ctypes.byref(n)) != 0:
+        raise RuntimeError("rrf_gemm_profile_emulated failed")
+    return ms.value, fl.value, tf.value, n.value
 
 
 def mlp_param_count() -> int:

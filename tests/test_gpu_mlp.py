@@ -78,10 +78,17 @@ def test_policy_inside_randutv_keeps_an_exact_factorization():
     qs = rrf.opts_q_used(opts)[: steps - 1]
     assert all(0 <= q <= 3 for q in qs)
     F = rrf.opts_features(opts)[: steps - 1]
-    assert np.all(np.isfinite(F)) and np.all(F[:, 15] == 1.0)
-    # the features reproduce the policy's choices through the standalone forward kernel
-    zq = rrf.mlp_forward(p16, torch.from_numpy(F).cuda()).argmax(1).cpu().numpy()
-    assert list(zq) == qs
+    assert np.all(np.isfinite(F)) and np.all(np.abs(F) <= 30)
+    # f13..f15 use the previous step's singular values, which end up on the diagonal of T
+    assert np.all(F[0, 13:16] == 0.0)
+    d = np.abs(np.diag(T))
+    for i in range(2, steps):
+        D = d[(i - 2) * b:(i - 1) * b]
+        assert abs(F[i - 1, 14] - np.log10(D[-1] / D[0])) <= 1e-5 * (1 + abs(F[i - 1, 14]))
+    # the features reproduce the policy's choices through the standalone forward kernel and the
+    # cumulative-probability rule
+    z = rrf.mlp_forward(p16, torch.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
+    assert list(qpolicy.decide(z)) == qs
 
 
 def test_features_without_parameters_fall_back_to_q():
@@ -95,9 +102,9 @@ def test_features_without_parameters_fall_back_to_q():
     assert torch.equal(T, T2)
 
 
-def _policy_vs_fixed(params, count=8, n=1024, b=128, target=1.1):
-    """Learned policy against fixed q = 2 on held-out matrices (seeds the training set never used):
-    per boundary e_k and sigma_{k+1}, power iterations spent."""
+def _policy_vs_fixed(params, count=8, n=1024, b=128, with_q3=False):
+    """Learned policy against fixed q = 2 (and q = 3) on held-out matrices (seeds the training set never
+    used): per boundary (matrix, i, q chosen, e_k learned, e_k q=2, sigma_{k+1}, e_k q=3)."""
     steps = n // b
     rows = []
     for t in range(count):
@@ -105,19 +112,20 @@ def _policy_vs_fixed(params, count=8, n=1024, b=128, target=1.1):
         opts = rrf.make_opts(q_policy=rrf.Q_LEARNED, mlp_params=params, steps=steps)
         _, TL, _ = rrf.randutv(A, b, 2, seed=5, opts=opts)
         _, TF, _ = rrf.randutv(A, b, 2, seed=5)
+        T3 = rrf.randutv(A, b, 3, seed=5)[1] if with_q3 else None
         qs = rrf.opts_q_used(opts)[: steps - 1]
         for i in range(1, steps):
             el = qpolicy.spectral_norm(torch, TL[i * b:, i * b:])
             ef = qpolicy.spectral_norm(torch, TF[i * b:, i * b:])
-            rows.append((t, i, qs[i - 1], el, ef, float(s[i * b])))
+            e3 = qpolicy.spectral_norm(torch, T3[i * b:, i * b:]) if with_q3 else float("nan")
+            rows.append((t, i, qs[i - 1], el, ef, float(s[i * b]), e3))
     return rows
 
 
 def test_trained_policy_gains_over_fixed_q2():
     """The packaged network (trained on matrices the method factored itself) against the fallback q = 2 on
-    held-out matrices of mixed decay: fewer power iterations in total, and at least as many block
-    boundaries meeting the quality target e_k <= 1.1 sigma_{k+1} less one; where the learned step misses
-    the target it stays within 25 % of the fallback's e_k."""
+    held-out matrices of mixed decay: fewer power iterations in total, at least as many block boundaries
+    meeting the quality target e_k <= 1.1 sigma_{k+1}, and no boundary more than 3x the fallback's e_k."""
     params = qpolicy.load()
     if params is None:
         pytest.skip("no trained policy packaged")
@@ -126,9 +134,9 @@ def test_trained_policy_gains_over_fixed_q2():
     q_fixed = 2 * len(rows)
     hit_l = sum(r[3] <= 1.1 * r[5] for r in rows)
     hit_f = sum(r[4] <= 1.1 * r[5] for r in rows)
-    print(f"power iterations learned {q_learned} / fixed {q_fixed}; boundaries on target learned {hit_l} / "
-          f"fixed {hit_f} of {len(rows)}")
+    worst = max(r[3] / r[4] for r in rows)
+    print(f"power iterations learned {q_learned} / fixed {q_fixed}; on target learned {hit_l} / fixed {hit_f} "
+          f"of {len(rows)}; worst e_k learned / fixed {worst:.3f}")
     assert q_learned < q_fixed
-    assert hit_l >= hit_f - 1
-    for t, i, q, el, ef, sg in rows:
-        assert el <= 1.1 * sg or el <= 1.25 * ef, (t, i, q, el, ef, sg)
+    assert hit_l >= hit_f
+    assert worst <= 3.0
