@@ -18,7 +18,7 @@
 // C = alpha 2^(e_r + f_c - 48) (acc + frac) + beta C in FP64.
 //
 // Kernel (576 threads, persistent over 128 x 32 output tiles x K splits): warp 0 lane 0 loads the 7 + 7
-// digit tiles of each 32-wide K chunk with TMA (64-byte swizzle, 3-stage ring); warp 1 lane 0 issues, per
+// digit tiles of each 32-wide K chunk with two 3-D TMA loads (64-byte swizzle, 3-stage ring); warp 1 lane 0 issues, per
 // 16-wide K step and A digit a, one MMA of A_a against the B digits 0..6-a laid back to back (N = (7-a) 32),
 // into two TMEM accumulator buffers of 7 x 32 columns used alternately; warps 2..17 read a buffer
 // (tcgen05.ld) while the MMAs fill the other.  All mbarrier waits are bounded (RRF_TIMEOUT, drain, free
@@ -113,10 +113,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return false;
   return true;
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+// All 7 digit slices of a tile in one load: box (32 of K, rows, 7 slices), slices stacked in shared memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 // K-major, 64-byte swizzle: 8-row groups 512 bytes apart.
@@ -210,10 +211,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* st = smem + s * kStageBytes;
           mbar_expect_tx(&full_bar[s], kStageBytes);
           const int kx = (int)(k0 + (int64_t)i * KC);
-          for (int sl = 0; sl < kS; ++sl) {
-            tma_load_2d(st + sl * kTileA, &map_a, &full_bar[s], kx, (int)(sl * p.M + m0));
-            tma_load_2d(st + kS * kTileA + sl * kTileB, &map_b, &full_bar[s], kx, (int)(sl * p.N + n0));
-          }
+          tma_load_3d(st, &map_a, &full_bar[s], kx, (int)m0, 0);
+          tma_load_3d(st + kS * kTileA, &map_b, &full_bar[s], kx, (int)n0, 0);
           issued = g + 1;
         }
       }
@@ -341,60 +340,85 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
 }
 
+// The splitting works on the bit patterns with integer instructions only (the FP64 pipe of this GPU is
+// ~60x slower than its integer pipe).  |x| orders like the bit pattern with the sign cleared.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// e with |x| < 2^(e - 1) for the largest magnitude m (bit pattern, nonzero): frexp exponent + 1.
+__device__ __forceinline__ int scale_exponent(unsigned long long m) {
+  if (m == 0) return 0;
+  const int E = (int)(m >> 52);
+  if (E != 0) return E - 1021;
+  return (64 - __clzll((long long)m)) - 1074 + 1;  // subnormal: m * 2^-1074
+}
+
 // Row exponents: e_r with max_k |X(r, k)| < 2^(e_r - 1) (0 for an all-zero row).  X(r, k) = X[r sr + k sk].
 __global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restrict__ X, int64_t sr, int64_t sk,
                                  int* __restrict__ e) {
   if (sr == 1) {  // rows contiguous in memory across threads
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-      double mx = 0.0;
-      for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(X[r + k * sk]));
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      e[r] = mx > 0.0 ? ex + 1 : 0;
+      unsigned long long mx = 0;
+      for (int64_t k = 0; k < K; ++k) mx = max(mx, abs_bits(X[r + k * sk]));
+      e[r] = scale_exponent(mx);
     }
   } else {  // each row contiguous: one warp per row
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = wid; r < rows; r += nw) {
-      double mx = 0.0;
-      for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[r * sr + k]));
+      unsigned long long mx = 0;
+      for (int64_t k = lane; k < K; k += 32) mx = max(mx, abs_bits(X[r * sr + k]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
-        e[r] = mx > 0.0 ? ex + 1 : 0;
-      }
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) e[r] = scale_exponent(mx);
     }
   }
 }
 
 // Digits: D[s][r][k] (row stride Kp, slice stride rows * Kp), zero for k >= K.  32 x 32 tiles.
+// x 2^(56 - e_r) is rounded to an integer X (|X| < 2^55; what it drops is below 2^-57 2^e_r) and X is
+// written in balanced base 256: X = sum_s d_s 2^(8 (6 - s)), |d_s| <= 128.
 __global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const double* __restrict__ X, int64_t sr,
                                 int64_t sk, const int* __restrict__ e, __nv_bfloat16* __restrict__ D) {
-  __shared__ double tile[32][33];
+  __shared__ long long tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32, kb = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int j = ty; j < 32; j += 8) {
     // read with the contiguous index on tx
     int64_t r, k;
     if (sr == 1) { r = r0 + tx; k = kb + j; } else { r = r0 + j; k = kb + tx; }
-    const double v = (r < rows && k < K) ? X[r * sr + k * sk] : 0.0;
+    const long long v = (r < rows && k < K) ? __double_as_longlong(X[r * sr + k * sk]) : 0ll;
     if (sr == 1) tile[tx][j] = v; else tile[j][tx] = v;  // tile[row][k]
   }
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
     const int64_t r = r0 + j, k = kb + tx;
     if (r >= rows || k >= Kp) continue;
-    double t = ldexp(tile[j][tx], -e[r]);
-#pragma unroll
-    for (int s = 0; s < kS; ++s) {
-      t *= 256.0;
-      const double dg = rint(t);
-      t -= dg;
-      D[((int64_t)s * rows + r) * Kp + k] = __double2bfloat16(dg);
+    const unsigned long long bits = (unsigned long long)tile[j][tx];
+    const unsigned long long a = bits & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(a >> 52);
+    long long mant = (long long)(a & 0xFFFFFFFFFFFFFull);
+    int sh;
+    if (E != 0) {
+      mant |= 1ll << 52;
+      sh = E - 1075 + 56 - e[r];
+    } else {
+      sh = -1074 + 56 - e[r];
     }
+    long long Xi;
+    if (a == 0 || sh <= -64) Xi = 0;
+    else if (sh >= 0) Xi = mant << min(sh, 62);  // |x| < 2^(e - 1) keeps Xi below 2^55
+    else Xi = (mant + (1ll << (-sh - 1))) >> (-sh);
+    if (bits >> 63) Xi = -Xi;
+#pragma unroll
+    for (int sl = 0; sl < kS - 1; ++sl) {
+      const int sb = 8 * (kS - 1 - sl);
+      const long long dg = (Xi + (1ll << (sb - 1))) >> sb;
+      Xi -= dg << sb;
+      D[((int64_t)sl * rows + r) * Kp + k] = __float2bfloat16_rn((float)dg);
+    }
+    D[((int64_t)(kS - 1) * rows + r) * Kp + k] = __float2bfloat16_rn((float)Xi);
   }
 }
 
@@ -429,14 +453,16 @@ EncodeTiledFn oz_encode_fn() {
   return fn;
 }
 
-bool oz_map(CUtensorMap* map, const void* base, int64_t rows_total, int64_t Kp, int box_rows) {
+// 3-D map over the digit slices D[s][r][k]: dims (Kp, rows, 7); a box is (32, box_rows, 7) and lands in
+// shared memory as 7 stacked (box_rows x 32) tiles with the 64-byte swizzle.  Rows past `rows` read zeros.
+bool oz_map(CUtensorMap* map, const void* base, int64_t rows, int64_t Kp, int box_rows) {
   EncodeTiledFn fn = oz_encode_fn();
   if (fn == nullptr || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((Kp * 2) & 15) != 0) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows_total};
-  cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)kS};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)box_rows, (cuuint32_t)kS};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -531,7 +557,7 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
                                                                                             eb, Bs);
   count_launch();
   CUtensorMap ma, mb;
-  if (!oz_map(&ma, As, kS * M, Kp, BM) || !oz_map(&mb, Bs, kS * N, Kp, BN)) return cudaErrorInvalidValue;
+  if (!oz_map(&ma, As, M, Kp, BM) || !oz_map(&mb, Bs, N, Kp, BN)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());

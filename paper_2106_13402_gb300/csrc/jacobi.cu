@@ -312,10 +312,11 @@ __global__ void __launch_bounds__(kPreThreads, 1)
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float cs = 1.f / sqrtf(1.f + tt * tt);
+        // approximate division / square roots suffice here: the FP64 sweeps decide the result
+        if (ga != 0.f && ga * ga > tol * tol * (al * be)) {
+          const float zeta = __fdividef(be - al, 2.f * ga);
+          const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+          const float cs = rsqrtf(fmaf(tt, tt, 1.f));
           const float sn = cs * tt;
           float* vp = Vs + p * c;
           float* vq = Vs + q * c;

@@ -41,7 +41,7 @@ size_t layout(int64_t m, int64_t n, int64_t b, int gemm_mode, Arena& ar, PWs& w)
   w.eng.scratch = w.gemm;
   w.eng.scratch_bytes = w.gemm_bytes;
   w.eng.status = w.hdr ? &w.hdr->status : nullptr;
-  w.eng.emulate = gemm_mode == RRF_GEMM_EMULATED;
+  w.eng.emulate = gemm_mode != RRF_GEMM_NATIVE;
   w.eng.force = gemm_mode == RRF_GEMM_EMULATED;
   if (w.eng.emulate) {
     w.eng.oz_bytes = ozaki_bound(m, n, b);
