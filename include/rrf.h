@@ -61,7 +61,7 @@ enum { RRF_SKETCH_FP64 = 0, RRF_SKETCH_BF16 = 1 };
 /* How the power-iteration count q of each randUTV step is chosen. */
 enum { RRF_Q_FIXED = 0, RRF_Q_LEARNED = 1 };
 
-/* How the FP64 products run.  RRF_GEMM_AUTO (default): products of at least 2e8 flops whose short side is
+/* How the FP64 products run.  RRF_GEMM_AUTO (default): products of at least 2e7 flops whose short side is
  * >= 64, long side >= 128 and inner size >= 32 use the FP64 emulation on the BF16 tensor cores
  * (rrf_gemm_emulated, exact digit products, error relative to row / column maxima), the rest the DFMA
  * kernel.  RRF_GEMM_NATIVE: the DFMA kernel for every product (the plain FP64 method).

@@ -353,25 +353,34 @@ __device__ __forceinline__ int scale_exponent(unsigned long long m) {
   return (64 - __clzll((long long)m)) - 1074 + 1;  // subnormal: m * 2^-1074
 }
 
-// Row exponents: e_r with max_k |X(r, k)| < 2^(e_r - 1) (0 for an all-zero row).  X(r, k) = X[r sr + k sk].
-__global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restrict__ X, int64_t sr, int64_t sk,
-                                 int* __restrict__ e) {
-  if (sr == 1) {  // rows contiguous in memory across threads
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-      unsigned long long mx = 0;
-      for (int64_t k = 0; k < K; ++k) mx = max(mx, abs_bits(X[r + k * sk]));
-      e[r] = scale_exponent(mx);
+// Row maxima (as bit patterns with the sign cleared) of X(r, k) = X[r sr + k sk]; mx must be zeroed first.
+// sr == 1 (a row strided in memory): 32 rows x a slice of K per block, combined with atomicMax; otherwise
+// (each row contiguous) one warp per row.
+__global__ void oz_rowmax_kernel(int64_t rows, int64_t K, const double* __restrict__ X, int64_t sr, int64_t sk,
+                                 unsigned long long* __restrict__ mx) {
+  if (sr == 1) {
+    __shared__ unsigned long long red[8][32];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
+    unsigned long long m = 0;
+    if (r < rows)
+      for (int64_t k = (int64_t)blockIdx.y * 8 + ty; k < K; k += (int64_t)gridDim.y * 8) m = max(m, abs_bits(X[r + k * sk]));
+    red[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0 && r < rows) {
+      for (int j = 1; j < 8; ++j) m = max(m, red[j][tx]);
+      if (m != 0) atomicMax(&mx[r], m);
     }
-  } else {  // each row contiguous: one warp per row
+  } else {
     const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t wid = (blockIdx.x * (int64_t)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x * blockDim.y) >> 5;
     for (int64_t r = wid; r < rows; r += nw) {
-      unsigned long long mx = 0;
-      for (int64_t k = lane; k < K; k += 32) mx = max(mx, abs_bits(X[r * sr + k]));
+      unsigned long long m = 0;
+      for (int64_t k = lane; k < K; k += 32) m = max(m, abs_bits(X[r * sr + k]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) e[r] = scale_exponent(mx);
+      for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) mx[r] = m;
     }
   }
 }
@@ -379,8 +388,10 @@ __global__ void oz_rowexp_kernel(int64_t rows, int64_t K, const double* __restri
 // Digits: D[s][r][k] (row stride Kp, slice stride rows * Kp), zero for k >= K.  32 x 32 tiles.
 // x 2^(56 - e_r) is rounded to an integer X (|X| < 2^55; what it drops is below 2^-57 2^e_r) and X is
 // written in balanced base 256: X = sum_s d_s 2^(8 (6 - s)), |d_s| <= 128.
+// Also writes the row exponents e_r (max_k |X(r, k)| < 2^(e_r - 1), 0 for an all-zero row) from the maxima.
 __global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const double* __restrict__ X, int64_t sr,
-                                int64_t sk, const int* __restrict__ e, __nv_bfloat16* __restrict__ D) {
+                                int64_t sk, const unsigned long long* __restrict__ mx, int* __restrict__ e,
+                                __nv_bfloat16* __restrict__ D) {
   __shared__ long long tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32, kb = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -395,6 +406,8 @@ __global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const doubl
   for (int j = ty; j < 32; j += 8) {
     const int64_t r = r0 + j, k = kb + tx;
     if (r >= rows || k >= Kp) continue;
+    const int er = scale_exponent(mx[r]);
+    if (blockIdx.y == 0 && tx == 0) e[r] = er;
     const unsigned long long bits = (unsigned long long)tile[j][tx];
     const unsigned long long a = bits & 0x7FFFFFFFFFFFFFFFull;
     const int E = (int)(a >> 52);
@@ -402,9 +415,9 @@ __global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const doubl
     int sh;
     if (E != 0) {
       mant |= 1ll << 52;
-      sh = E - 1075 + 56 - e[r];
+      sh = E - 1075 + 56 - er;
     } else {
-      sh = -1074 + 56 - e[r];
+      sh = -1074 + 56 - er;
     }
     long long Xi;
     if (a == 0 || sh <= -64) Xi = 0;
@@ -482,7 +495,7 @@ int oz_splits(int64_t M, int64_t N, int64_t Kp) {
 
 bool ozaki_eligible(const GemmDesc& d, bool force) {
   const int64_t lo = std::min(d.M, d.N), hi = std::max(d.M, d.N);
-  return hi >= 128 && lo >= 64 && d.K >= 32 && (force || 2.0 * d.M * d.N * d.K >= 2.0e8);
+  return hi >= 128 && lo >= 64 && d.K >= 32 && (force || 2.0 * d.M * d.N * d.K >= 2.0e7);
 }
 
 size_t ozaki_bound(int64_t m, int64_t n, int64_t b) {
@@ -524,6 +537,7 @@ size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K) {
   const int64_t Kp = (K + KC - 1) / KC * KC;
   size_t b = align_up((size_t)kS * M * Kp * 2, 256) + align_up((size_t)kS * N * Kp * 2, 256);
   b += align_up(sizeof(int) * M, 256) + align_up(sizeof(int) * N, 256);
+  b += align_up(sizeof(unsigned long long) * (M + N), 256);
   b += align_up((size_t)oz_splits(M, N, Kp) * M * N * sizeof(double), 256);
   return b;
 }
@@ -540,21 +554,31 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(take((size_t)kS * N * Kp * 2));
   int* ea = reinterpret_cast<int*>(take(sizeof(int) * M));
   int* eb = reinterpret_cast<int*>(take(sizeof(int) * N));
+  unsigned long long* mxa = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * (M + N)));
+  unsigned long long* mxb = mxa + M;
   const int splits = oz_splits(M, N, Kp);
   double* part = reinterpret_cast<double*>(take((size_t)splits * M * N * sizeof(double)));
   // op(A)(m, k) = A[m + k lda] or A[k + m lda]; op(B)^T(n, k) = op(B)(k, n) = B[k + n ldb] or B[n + k ldb]
   const int64_t asr = d.ta ? d.lda : 1, ask = d.ta ? 1 : d.lda;
   const int64_t bsr = d.tb ? 1 : d.ldb, bsk = d.tb ? d.ldb : 1;
   const int sms = dev_info().sms;
-  oz_rowexp_kernel<<<sms * 8, 256, 0, s>>>(M, K, d.A, asr, ask, ea);
-  count_launch();
-  oz_rowexp_kernel<<<sms * 8, 256, 0, s>>>(N, K, d.B, bsr, bsk, eb);
-  count_launch();
+  cudaError_t e0 = cudaMemsetAsync(mxa, 0, sizeof(unsigned long long) * (M + N), s);
+  if (e0 != cudaSuccess) return e0;
+  const unsigned kslices = (unsigned)std::min<int64_t>(std::max<int64_t>((K + 255) / 256, 1), 64);
+  auto rowmax = [&](int64_t rows, const double* X, int64_t sr, int64_t sk, unsigned long long* mx) {
+    if (sr == 1)
+      oz_rowmax_kernel<<<dim3((unsigned)((rows + 31) / 32), kslices), dim3(32, 8), 0, s>>>(rows, K, X, sr, sk, mx);
+    else
+      oz_rowmax_kernel<<<(unsigned)(sms * 8), dim3(32, 8), 0, s>>>(rows, K, X, sr, sk, mx);
+    count_launch();
+  };
+  rowmax(M, d.A, asr, ask, mxa);
+  rowmax(N, d.B, bsr, bsk, mxb);
   oz_split_kernel<<<dim3((unsigned)((M + 31) / 32), (unsigned)(Kp / 32)), dim3(32, 8), 0, s>>>(M, K, Kp, d.A, asr, ask,
-                                                                                            ea, As);
+                                                                                            mxa, ea, As);
   count_launch();
   oz_split_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)(Kp / 32)), dim3(32, 8), 0, s>>>(N, K, Kp, d.B, bsr, bsk,
-                                                                                            eb, Bs);
+                                                                                            mxb, eb, Bs);
   count_launch();
   CUtensorMap ma, mb;
   if (!oz_map(&ma, As, M, Kp, BM) || !oz_map(&mb, Bs, N, Kp, BN)) return cudaErrorInvalidValue;

@@ -2,7 +2,7 @@
 // the last block), on one thread-block cluster.
 //
 // FP64 on GB300 runs at ~2 DFMA/clk/SM, so a single SM would need ~10 ms for a 128 x 128 SVD; the
-// cluster spreads the rows of M and of the accumulated V over CL CTAs (distributed shared memory):
+// cluster spreads the rows of M and of the accumulated V over CL = 16 (or 8) CTAs (distributed shared memory):
 // each CTA computes its partial column norms / inner products for all pairs of one round, the
 // partials are summed in rank order through DSMEM after one cluster barrier, every CTA derives the
 // identical rotation, and applies it to its own rows.  Pairs follow the round-robin (tournament)
@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "rrf_internal.cuh"
 
@@ -24,7 +25,6 @@ namespace cg = cooperative_groups;
 namespace rrf {
 namespace {
 
-constexpr int CL = 8;
 constexpr int NT = 256;
 constexpr int kMaxC = 256;
 constexpr int kMaxSweeps = 40;
@@ -58,8 +58,9 @@ __device__ __forceinline__ void round_pair(int t, int k, int ne, int& p, int& q)
   q = max(a, b);
 }
 
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
-    jacobi_kernel(const __grid_constant__ JacobiArgs a) {
+// CL: cluster size (16 where the GPU schedules such clusters, else 8), given again at launch.
+template <int CL>
+__global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ JacobiArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ double smem[];
@@ -71,6 +72,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
   double* vmax = nrm + kMaxC;                     // [kMaxC] partial max |v|
   int* vidx = reinterpret_cast<int*>(vmax + kMaxC);  // [kMaxC] row of the max
   __shared__ int s_rot;
+  __shared__ double s_cs[kMaxC / 2], s_sn[kMaxC / 2];
+  __shared__ int s_rotf[kMaxC / 2];
   __shared__ double s_sig[kMaxC];
   __shared__ double s_sign[kMaxC];
   __shared__ int s_rank[kMaxC];
@@ -138,33 +141,40 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
         }
       }
       cluster.sync();
-      // (3) one lane per pair derives the rotation (FP64 division and square roots are scarce on this
-      // GPU, so the other lanes of the pair only receive cs, sn by shuffle), then all lanes rotate.
-      double cs = 1.0, sn = 0.0;
-      int rot = 0;
-      if (real && sub == 0) {
-        double A = 0.0, B = 0.0, G = 0.0;
+      // (3) thread g < npairs sums pair g's partials in rank order and derives its rotation, so these FP64
+      // sequences (division, square roots) run in npairs / 32 fully active warps rather than in every warp
+      // with one active lane per pair: on this GPU's narrow FP64 pipe a warp instruction costs the same
+      // whatever its active lanes.  Results go through shared memory to the lanes that rotate.
+      if (tid < npairs) {
+        int gp, gq;
+        round_pair(t, tid, ne, gp, gq);
+        double gcs = 1.0, gsn = 0.0;
+        int grot = 0;
+        if (gq < c) {
+          double A = 0.0, B = 0.0, G = 0.0;
 #pragma unroll
-        for (int rr = 0; rr < CL; ++rr) {
-          const double* rp3 = part + ((size_t)(par * CL + rr) * (kMaxC / 2) + grp) * 3;
-          A += rp3[0];
-          B += rp3[1];
-          G += rp3[2];
+          for (int rr = 0; rr < CL; ++rr) {
+            const double* rp3 = part + ((size_t)(par * CL + rr) * (kMaxC / 2) + tid) * 3;
+            A += rp3[0];
+            B += rp3[1];
+            G += rp3[2];
+          }
+          if (G != 0.0 && fabs(G) > tol * sqrt(A * B)) {
+            const double zeta = (B - A) / (2.0 * G);
+            const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            gcs = 1.0 / sqrt(1.0 + tt * tt);
+            gsn = gcs * tt;
+            grot = 1;
+            s_rot = 1;
+          }
         }
-        if (G != 0.0 && fabs(G) > tol * sqrt(A * B)) {
-          const double zeta = (B - A) / (2.0 * G);
-          const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          cs = 1.0 / sqrt(1.0 + tt * tt);
-          sn = cs * tt;
-          rot = 1;
-        }
+        s_cs[tid] = gcs;
+        s_sn[tid] = gsn;
+        s_rotf[tid] = grot;
       }
-      if (tpp > 1) {
-        const int leader = (threadIdx.x & 31) & ~(tpp - 1);
-        cs = __shfl_sync(0xffffffffu, cs, leader);
-        sn = __shfl_sync(0xffffffffu, sn, leader);
-        rot = __shfl_sync(0xffffffffu, rot, leader);
-      }
+      __syncthreads();
+      const double cs = active ? s_cs[grp] : 1.0, sn = active ? s_sn[grp] : 0.0;
+      const int rot = active ? s_rotf[grp] : 0;
       if (real && rot) {
         double* mp = Ml + p * ldl;
         double* mq = Ml + q * ldl;
@@ -178,7 +188,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
           vp[i] = cs * u - sn * v;
           vq[i] = sn * u + cs * v;
         }
-        if (sub == 0) atomicAdd(&s_rot, 1);
       }
       par ^= 1;
       __syncthreads();
@@ -256,24 +265,36 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT)
 }
 
 // FP32 pre-pass (c <= 128, one CTA): Hestenes sweeps on R 2^-e (scaled into FP32 range) in shared memory,
-// one warp per column pair, until a sweep without rotations at tolerance 2^-16 or kPreSweeps sweeps (the
-// FP64 sweeps converge quadratically from there: 2^-16 -> 2^-32 -> below c 2^-53).  Only the
-// accumulated rotation V32 leaves the kernel: it is a preconditioner, orthonormalized in FP64 afterwards,
-// and the FP64 sweeps that follow decide the result.
+// one warp per column pair (each lane holds 4 consecutive rows as a float4; columns padded to 128 rows
+// with zeros), until a sweep without rotations at tolerance 2^-16 or kPreSweeps sweeps (a looser tolerance
+// costs FP64 sweeps when singular values cluster, a tighter one meets FP32 rounding).  Only the accumulated rotation
+// V32 leaves the kernel: it is a preconditioner, orthonormalized in FP64 afterwards.
 constexpr int kPreThreads = 1024;
 constexpr int kPreMinC = 32;
 constexpr int kPreMaxC = 128;
 constexpr int kPreSweeps = 10;
+constexpr int kPreLd = kPreMaxC;  // column stride (floats)
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 __global__ void __launch_bounds__(kPreThreads, 1)
     jacobi_f32_prepass_kernel(int c, const double* __restrict__ M, int64_t ldm, double* __restrict__ Vout,
-                              int64_t ldvo) {
-  extern __shared__ float sm32[];
-  float* Ms = sm32;          // [c][c], column k at k * c
-  float* Vs = sm32 + c * c;  // [c][c]
+                              int64_t ldvo, int* sweeps_out) {
+  extern __shared__ __align__(16) float sm32[];
+  float* Ms = sm32;                  // [c][kPreLd], column k at k * kPreLd, rows >= c zero
+  float* Vs = sm32 + c * kPreLd;     // [c][kPreLd]
+  __shared__ unsigned char s_pair[kPreMaxC - 1][kPreMaxC / 2][2];
   __shared__ double s_part[kPreThreads / 32];
   __shared__ int s_rot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ne = c + (c & 1), npairs = ne / 2, rounds = ne - 1;
+  for (int idx = tid; idx < rounds * npairs; idx += kPreThreads) {
+    int p, q;
+    round_pair(idx / npairs, idx % npairs, ne, p, q);
+    s_pair[idx / npairs][idx % npairs][0] = (unsigned char)p;
+    s_pair[idx / npairs][idx % npairs][1] = (unsigned char)q;
+  }
   double mx = 0.0;
   for (int idx = tid; idx < c * c; idx += kPreThreads) mx = fmax(mx, fabs(M[(idx % c) + (int64_t)(idx / c) * ldm]));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -283,51 +304,45 @@ __global__ void __launch_bounds__(kPreThreads, 1)
   for (int w = 0; w < kPreThreads / 32; ++w) mx = fmax(mx, s_part[w]);
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
-  for (int idx = tid; idx < c * c; idx += kPreThreads) {
-    const int i = idx % c, k = idx / c;
-    Ms[idx] = (float)ldexp(M[i + (int64_t)k * ldm], -ex);
+  for (int idx = tid; idx < c * kPreLd; idx += kPreThreads) {
+    const int i = idx % kPreLd, k = idx / kPreLd;
+    Ms[idx] = (i < c) ? (float)ldexp(M[i + (int64_t)k * ldm], -ex) : 0.f;
     Vs[idx] = (i == k) ? 1.f : 0.f;
   }
   if (tid == 0) s_rot = 0;
   __syncthreads();
-  const int ne = c + (c & 1), npairs = ne / 2, rounds = ne - 1;
-  const float tol = 0x1p-16f;
-  for (int sweep = 0; sweep < kPreSweeps; ++sweep) {
+  const float tol2 = 0x1p-32f;  // tolerance 2^-16, squared
+  const int r4 = 4 * lane;
+  int sweep = 0;
+  for (; sweep < kPreSweeps; ++sweep) {
     for (int t = 0; t < rounds; ++t) {
       for (int g = warp; g < npairs; g += kPreThreads / 32) {
-        int p, q;
-        round_pair(t, g, ne, p, q);
+        const int p = s_pair[t][g][0], q = s_pair[t][g][1];
         if (q >= c) continue;
-        float* mp = Ms + p * c;
-        float* mq = Ms + q * c;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < c; i += 32) {
-          const float x = mp[i], y = mq[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
-        }
+        float* mp = Ms + p * kPreLd + r4;
+        float* mq = Ms + q * kPreLd + r4;
+        const float4 x = ld4(mp), y = ld4(mq);
+        float al = x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+        float be = y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+        float ga = x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
         for (int o = 16; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
         // approximate division / square roots suffice here: the FP64 sweeps decide the result
-        if (ga != 0.f && ga * ga > tol * tol * (al * be)) {
+        if (ga != 0.f && ga * ga > tol2 * (al * be)) {
           const float zeta = __fdividef(be - al, 2.f * ga);
           const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
           const float cs = rsqrtf(fmaf(tt, tt, 1.f));
           const float sn = cs * tt;
-          float* vp = Vs + p * c;
-          float* vq = Vs + q * c;
-          for (int i = lane; i < c; i += 32) {
-            const float x = mp[i], y = mq[i];
-            mp[i] = cs * x - sn * y;
-            mq[i] = sn * x + cs * y;
-            const float u = vp[i], v = vq[i];
-            vp[i] = cs * u - sn * v;
-            vq[i] = sn * u + cs * v;
-          }
+          st4(mp, make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w));
+          st4(mq, make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w));
+          float* vp = Vs + p * kPreLd + r4;
+          float* vq = Vs + q * kPreLd + r4;
+          const float4 u = ld4(vp), v = ld4(vq);
+          st4(vp, make_float4(cs * u.x - sn * v.x, cs * u.y - sn * v.y, cs * u.z - sn * v.z, cs * u.w - sn * v.w));
+          st4(vq, make_float4(sn * u.x + cs * v.x, sn * u.y + cs * v.y, sn * u.z + cs * v.z, sn * u.w + cs * v.w));
           if (lane == 0) s_rot = 1;
         }
       }
@@ -339,7 +354,9 @@ __global__ void __launch_bounds__(kPreThreads, 1)
     if (tid == 0) s_rot = 0;
     __syncthreads();
   }
-  for (int idx = tid; idx < c * c; idx += kPreThreads) Vout[(idx % c) + (int64_t)(idx / c) * ldvo] = (double)Vs[idx];
+  if (tid == 0 && sweeps_out != nullptr) *sweeps_out = sweep;  // diagnostics
+  for (int idx = tid; idx < c * c; idx += kPreThreads)
+    Vout[(idx % c) + (int64_t)(idx / c) * ldvo] = (double)Vs[(idx % c) + (idx / c) * kPreLd];
 }
 
 // Gram-Schmidt completion of u_k for exactly-zero singular values (two passes against the columns
@@ -398,10 +415,64 @@ __global__ void __launch_bounds__(NT) complete_kernel(int c, double* Us, int64_t
   if (tid == 0) hdr->flags[0] = 0;
 }
 
-size_t jacobi_smem(int c) {
-  const int rp = (c + CL - 1) / CL;
-  return ((size_t)2 * c * (rp + 1) + 2 * CL * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
+size_t jacobi_smem(int c, int cl) {
+  const int rp = (c + cl - 1) / cl;
+  return ((size_t)2 * c * (rp + 1) + 2 * cl * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
          kMaxC * sizeof(int);
+}
+
+// 16-CTA clusters are not portable: use them when the device accepts the attribute and can schedule one.
+int jacobi_cluster_size() {
+  static int cl = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cl = 8;
+    if (cudaFuncSetAttribute(jacobi_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(jacobi_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)jacobi_smem(kMaxC, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = jacobi_smem(kMaxC, 16);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, jacobi_kernel<16>, &cfg) == cudaSuccess && n > 0) cl = 16;
+    cudaGetLastError();
+  });
+  return cl;
+}
+
+template <int CL>
+cudaError_t launch_jacobi(const JacobiArgs& a, int c, cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)jacobi_smem(kMaxC, CL));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = jacobi_smem(c, CL);
+  cfg.stream = stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_kernel<CL>, a);
 }
 
 }  // namespace
@@ -420,7 +491,9 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   if (c > kMaxC) return cudaErrorInvalidValue;
   JacobiArgs a;
   a.c = (int)c;
-  a.rp = (int)((c + CL - 1) / CL);
+  // 16 CTAs only pay off when each holds enough rows (c > 128); measured on GB300
+  const int cl = (c > 128) ? jacobi_cluster_size() : 8;
+  a.rp = (int)((c + cl - 1) / cl);
   a.M = M;
   a.ldm = ldm;
   a.Us = Us;
@@ -446,11 +519,12 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
     static bool attr_pre = false;
     if (!attr_pre) {
       e = cudaFuncSetAttribute(jacobi_f32_prepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(2 * kPreMaxC * kPreMaxC * sizeof(float)));
+                               (int)(2 * kPreMaxC * kPreLd * sizeof(float)));
       if (e != cudaSuccess) return e;
       attr_pre = true;
     }
-    jacobi_f32_prepass_kernel<<<1, kPreThreads, 2 * c * c * sizeof(float), stream>>>((int)c, M, ldm, X, c);
+    jacobi_f32_prepass_kernel<<<1, kPreThreads, 2 * c * kPreLd * sizeof(float), stream>>>((int)c, M, ldm, X, c,
+                                                                                    &hdr->flags[2]);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int it = 0; it < 2; ++it) {
@@ -483,18 +557,12 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
     a.V0 = X;
     a.ldv0 = c;
   }
-  const size_t smem = jacobi_smem((int)c);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxC));
-    attr = true;
-  }
   e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  jacobi_kernel<<<CL, NT, smem, stream>>>(a);
+  e = (cl == 16) ? launch_jacobi<16>(a, (int)c, stream) : launch_jacobi<8>(a, (int)c, stream);
   count_launch();
-  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   complete_kernel<<<1, NT, 0, stream>>>((int)c, Us, ldu, s, hdr);
   count_launch();
   return cudaGetLastError();

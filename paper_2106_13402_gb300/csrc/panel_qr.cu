@@ -136,13 +136,22 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
 
   for (int j = 0; j < w; ++j) {
     const int par = j & 1;
-    // Reduce the partial sums: warp per slot, lanes over CTAs (coalesced), fixed shuffle tree.
+    // Reduce the partial sums: 8 threads per slot (32 slots per pass), each adding every 8th CTA's
+    // partial with all its loads in flight, then a fixed 3-step shuffle tree -- deterministic, and one L2
+    // round trip per 32 slots instead of one per slot.
     const double* part = a.partials + (int64_t)par * w * a.nb;
-    for (int k = j + warp; k < w; k += NT / 32) {
+    for (int kb = j; kb < w; kb += NT / 8) {
+      const int k = kb + (tid >> 3), sub = tid & 7;
       double sum = 0.0;
-      for (int c = lane; c < a.nb; c += 32) sum += __ldcg(part + (int64_t)k * a.nb + c);
-      sum = warp_sum(sum);
-      if (lane == 0) red[k] = sum;
+      if (k < w) {
+        const double* pk = part + (int64_t)k * a.nb;
+#pragma unroll 4
+        for (int c = sub; c < a.nb; c += 8) sum += __ldcg(pk + c);
+      }
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+      if (k < w && sub == 0) red[k] = sum;
     }
     const double* row = a.rowbuf + (int64_t)par * w;
     for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);  // P(j, k)
