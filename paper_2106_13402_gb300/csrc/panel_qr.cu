@@ -222,22 +222,36 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
   }
 }
 
-// Forward recurrence for the compact-WY factor from S = Y^T Y (one CTA; w <= 256).
+// Forward recurrence for the compact-WY factor from S = Y^T Y (one CTA; w <= 256):
+//   Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j),  Tf(j, j) = tau_j.
+// For each column the 8 warps split the inner index l and the lanes cover the rows, so the FP64 chains
+// are j/8 long instead of j; partial sums are combined in warp order (deterministic).
 __global__ void __launch_bounds__(NT) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
                                                    const double* __restrict__ tau, double* Tf, int64_t ldt) {
   __shared__ double sc[kMaxW];
-  const int p = threadIdx.x;
+  __shared__ double part[NT / 32][kMaxW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
   for (int j = 0; j < w; ++j) {
-    if (p < w) sc[p] = S[p + (int64_t)j * lds];
+    for (int p = tid; p < j; p += NT) sc[p] = S[p + (int64_t)j * lds];
     __syncthreads();
-    if (p < w) {
+    const int l0 = (j * warp) / NW, l1 = (j * (warp + 1)) / NW;
+    for (int p = lane; p < j; p += 32) {
+      double acc = 0.0;
+      for (int l = max(l0, p); l < l1; ++l) acc = fma(Tf[p + (int64_t)l * ldt], sc[l], acc);
+      part[warp][p] = acc;
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    for (int p = tid; p < w; p += NT) {
       double v = 0.0;
       if (p < j) {
         double acc = 0.0;
-        for (int l = p; l < j; ++l) acc = fma(Tf[p + (int64_t)l * ldt], sc[l], acc);
-        v = -tau[j] * acc;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc += part[q][p];
+        v = -tj * acc;
       } else if (p == j) {
-        v = tau[j];
+        v = tj;
       }
       Tf[p + (int64_t)j * ldt] = v;
     }
@@ -266,7 +280,7 @@ size_t panel_scratch_bytes(int64_t r, int64_t w) {
 
 cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y, int64_t ldy,
                      double* Tf, int64_t ldtf, double* Rout, int64_t ldr, double* scratch,
-                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream) {
+                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream, const GemmEngine* eng) {
   if (w <= 0 || r <= 0) return cudaSuccess;
   if (w > kMaxW || r < w) return cudaErrorInvalidValue;
   const int nb = choose_nb(r);
@@ -320,7 +334,10 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
     g.A = Y; g.lda = ldy; g.ta = 1;
     g.B = Y; g.ldb = ldy; g.tb = 0;
     g.C = gram; g.ldc = w;
-    e = gemm_f64(&g, 1, reinterpret_cast<double*>(base + off), scratch_bytes - off, stream);
+    g.alpha = 1.0;
+    g.beta = 0.0;
+    e = (eng != nullptr) ? gemm_run(*eng, &g, 1, stream)
+                         : gemm_f64(&g, 1, reinterpret_cast<double*>(base + off), scratch_bytes - off, stream);
     if (e != cudaSuccess) return e;
     larft_kernel<<<1, NT, 0, stream>>>((int)w, gram, w, tau, Tf, ldtf);
     count_launch();

@@ -71,7 +71,7 @@ cudaError_t blocked_hqr(int64_t rows, int64_t cols, double* X, int64_t ldx, int6
     double* Yj = w.Ys + j0 + j0 * rows;
     double* Tj = w.Tall + (j0 / b) * b * b;
     cudaError_t e = panel_qr(rr, wd, X + j0 + j0 * ldx, ldx, w.tau + j0, Yj, rows, Tj, b, nullptr, 0,
-                             w.panel, w.panel_bytes, w.hdr, s);
+                             w.panel, w.panel_bytes, w.hdr, s, &w.eng);
     if (e != cudaSuccess) return e;
     const int64_t nc = cols - j0 - wd;
     if (nc <= 0) continue;

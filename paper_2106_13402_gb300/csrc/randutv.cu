@@ -152,7 +152,7 @@ cudaError_t apply_t22(bool transposed, int64_t r, int64_t c, int64_t b, const do
 
 // Orthonormal basis (explicit thin Q, rows x b) of X via the panel Householder QR; X is overwritten.
 cudaError_t orthonormalize(int64_t rows, int64_t b, double* X, double* Qout, const RWs& w, cudaStream_t s) {
-  cudaError_t e = panel_qr(rows, b, X, rows, w.tauu, w.Yu, rows, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s);
+  cudaError_t e = panel_qr(rows, b, X, rows, w.tauu, w.Yu, rows, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s, &w.eng);
   if (e == cudaSuccess) e = explicit_q(rows, b, w.Yu, w.Tu, w.Rs, Qout, w, s);
   return e;
 }
@@ -279,7 +279,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       if (learned) {
         // Features from the q = 0 sketch (the R of its Householder QR), MLP -> q for this step.
         RRF_CUDA_TRY(copy_matrix(c, b, w.Y, c, w.Qt, c, s));
-        RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s));
+        RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s, &w.eng));
         RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, i > 1 ? w.sig : nullptr, (int)i, (int)steps, n, c, w.feat, s));
         if (opts->mlp_params != nullptr) {
           RRF_CUDA_TRY(policy_decide(opts->mlp_params, w.feat, w.qdev, s));
@@ -304,7 +304,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       RRF_CUDA_TRY(sketch_continue(r, c, b, T22, ldt, qi, bf16, reorth, start, w, s));
       // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
       RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,
-                            w.hdr, s));
+                            w.hdr, s, &w.eng));
       {
         double* CT = T + o * ldt;
         double* CV = V + o * ldv;
@@ -320,7 +320,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       }
       // [U_i, R] = HQR_full(T(o:, o:o+b)).
       RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, w.Rs, b, w.panel, w.panel_bytes,
-                            w.hdr, s));
+                            w.hdr, s, &w.eng));
       {
         double* C = T + o + (o + b) * ldt;  // r x (c - b)
         double* CU = U + o * ldu;           // m x r
@@ -360,7 +360,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       int64_t ldm = ldt;
       if (r > c) {
         RRF_CUDA_TRY(panel_qr(r, c, T22, ldt, w.tauu, w.Yu, r, w.Tu, c, w.Rs, c, w.panel, w.panel_bytes,
-                              w.hdr, s));
+                              w.hdr, s, &w.eng));
         M = w.Rs;
         ldm = c;
       }

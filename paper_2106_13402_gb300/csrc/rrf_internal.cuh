@@ -122,9 +122,11 @@ size_t panel_scratch_bytes(int64_t r, int64_t w);
 // P (r x w, ld) overwritten with R / reflectors; writes tau, explicit Y (r x w), (if Tf != null)
 // the compact-WY factor and (if Rout != null) a w x w copy of R with zeros below the diagonal.
 // hdr: workspace header (barrier words + status).
+// eng (optional): GEMM router for the Gram matrix Y^T Y (else the DFMA kernel with `scratch`).
+struct GemmEngine;
 cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
                      int64_t ldy, double* Tf, int64_t ldtf, double* Rout, int64_t ldr, double* scratch,
-                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream);
+                     size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream, const GemmEngine* eng = nullptr);
 
 // ---- Jacobi SVD (jacobi.cu) -----------------------------------------------------------------------
 // One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.  With scratch of at least
