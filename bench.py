@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--gemm", default="auto", choices=["auto", "native", "emulated"],
                    help="FP64 products: library default, DFMA only, or emulated on the BF16 tensor cores")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 (DFMA) comparison run")
+    p.add_argument("--no-per-method", action="store_true", help="skip the per-method timing runs (profiling)")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                    help="c2: FP64 randUTV + powerURV 8192^2 (default); c3: BF16-sketch randUTV 16384^2, b=256, q=2; "
                         "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128")
@@ -242,7 +243,7 @@ def run_ours(args):
 
     # Per-method device times (one more run each, outside the timed region).
     per = {}
-    for name in methods:
+    for name in ([] if args.no_per_method else methods):
         f = testmats.flops_randutv(n, n, b, q) if name == "randutv" else testmats.flops_powerurv(n, n, q)
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
@@ -456,6 +457,8 @@ def run_c3_c5(args):
         return
     fast = rrf.make_opts(sketch_prec=rrf.SKETCH_BF16, q_policy=rrf.Q_FIXED if c3 else rrf.Q_LEARNED,
                          mlp_params=params, steps=0 if c3 else steps)
+    # c5 also times the learned policy with the FP64 sketch (products emulated on the tensor cores)
+    fast64 = None if c3 else rrf.make_opts(q_policy=rrf.Q_LEARNED, mlp_params=params, steps=steps)
     plain = rrf.make_opts(gemm_mode=rrf.GEMM_NATIVE)
     out = (rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev))
     ws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, fast), dev)
@@ -478,12 +481,27 @@ def run_c3_c5(args):
     ks = list(range(b, n, b)) if not c3 else [b, 16 * b, n // 2, n - 2 * b]
     r_fast = _boundary_ratios(torch, T, s, b, ks)
     del ws
+    learned64 = None
+    if fast64 is not None:
+        ws64 = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, fast64), dev)
+        rrf.randutv(A, b, q, 17, opts=fast64, ws=ws64, out=out)
+        ms64 = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=fast64, ws=ws64, out=out, check_status=False),
+                      args.steps)
+        q64 = rrf.opts_q_used(fast64)[: steps - 1]
+        r64 = _boundary_ratios(torch, out[1], s, b, ks)
+        learned64 = {"ms": round(ms64, 1), "value": round(1e3 / ms64, 5),
+                     "q_used": {"mean": round(sum(q64) / len(q64), 3), "hist": [q64.count(v) for v in range(4)]},
+                     "on_target": sum(1 for v in r64.values() if v <= 1.1)}
+        del ws64
     # plain FP64 (DFMA products, FP64 sketch, fixed q = 2): one timed run
     pws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, plain), dev)
     rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out)
     pms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out, check_status=False), 1)
     r_plain = _boundary_ratios(torch, out[1], s, b, ks)
     del pws
+    if learned64 is not None:
+        learned64["speedup_vs_plain"] = round(pms / learned64["ms"], 3)
+        learned64["worst_ratio_over_plain"] = round(max(r64[k] / r_plain[k] for k in r64), 4)
     flops = testmats.flops_randutv(n, n, b, q)
     peaks, peak_src = measured_peaks()
     peak = float(peaks["bf16_tflops_sustained"])
@@ -506,6 +524,7 @@ def run_c3_c5(args):
         "on_target": on_target(r_fast), "boundaries": len(ks),
         "worst_ratio_fast_over_plain": round(max(r_fast[k] / r_plain[k] for k in r_fast), 4),
         "q_used": None if c3 else {"mean": round(sum(qs) / len(qs), 3), "hist": [qs.count(v) for v in range(4)]},
+        "learned_fp64_sketch": learned64,
         "residual": res, "device_status": int(st), "clocks": clocks, "gpu_launches": int(launches),
         "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
                      "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,

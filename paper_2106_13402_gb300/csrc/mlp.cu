@@ -9,7 +9,9 @@
 // diagonal magnitudes |R(j, j)| approximate the energy of T22 beyond its first j sampled directions, and
 // from the singular values D of the previous step's b x b core, the exact spectrum just before the block):
 //   f0..f7 = log10(|R(k_j, k_j)| / |R(0, 0)|), k_j = (j + 1) b / 8 - 1       (decay inside the block)
-//   f8 = (i - 1) / steps, f9 = log2(n) / 16, f10 = log2(c) / 16            (where in the factorization)
+//   f8 = (i - 1) / steps                                                      (where in the factorization)
+//   f9 = f10 = 0: reserved.  Features that scale with n or c (such as log2 n) would put every size the
+//   network was not trained on outside its input range; size enters through f8 and the ratios below.
 //   f11 = log10(|R(b-1, b-1)| / |R(b/2, b/2)|)                              (decay at the block edge)
 //   f12 = mean_k log10(|R(k, k)| / |R(0, 0)|)
 //   f13 = log10(|R(0, 0)| / D(b-1))         (energy of T22 against the last singular value before it)
@@ -203,8 +205,8 @@ __global__ void features_kernel(const double* __restrict__ Rdiag_src, int64_t ld
     f[j] = lg(d(k) / d0);
   }
   f[8] = (float)(step - 1) / (float)steps;
-  f[9] = (float)(log2((double)n) / 16.0);
-  f[10] = (float)(log2((double)c) / 16.0);
+  f[9] = 0.f;
+  f[10] = 0.f;
   f[11] = lg(d(b - 1) / d(b / 2));
   double mean = 0.0;
   for (int k = 0; k < b; ++k) mean += log10(d(k) / d0);
