@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
   double* nrm = part + 2 * CL * (kMaxC / 2) * 3;  // [kMaxC] partial squared norms
   double* vmax = nrm + kMaxC;                     // [kMaxC] partial max |v|
   int* vidx = reinterpret_cast<int*>(vmax + kMaxC);  // [kMaxC] row of the max
-  __shared__ int s_rot;
+  __shared__ int s_rot, s_big;
   __shared__ double s_cs[kMaxC / 2], s_sn[kMaxC / 2];
   __shared__ int s_rotf[kMaxC / 2];
   __shared__ double s_sig[kMaxC];
@@ -91,7 +91,10 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
     else
       Vl[col * ldl + i] = (i < nloc && gi == col) ? 1.0 : 0.0;
   }
-  if (tid == 0) s_rot = 0;
+  if (tid == 0) {
+    s_rot = 0;
+    s_big = 0;
+  }
   cluster.sync();
 
   const int ne = c + (c & 1);
@@ -159,13 +162,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
             B += rp3[1];
             G += rp3[2];
           }
-          if (G != 0.0 && fabs(G) > tol * sqrt(A * B)) {
+          const double sab = sqrt(A * B);
+          if (G != 0.0 && fabs(G) > tol * sab) {
             const double zeta = (B - A) / (2.0 * G);
             const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             gcs = 1.0 / sqrt(1.0 + tt * tt);
             gsn = gcs * tt;
             grot = 1;
             s_rot = 1;
+            if (fabs(G) > 0x1p-30 * sab) s_big = 1;
           }
         }
         s_cs[tid] = gcs;
@@ -193,9 +198,16 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
       __syncthreads();
     }
     __syncthreads();
-    converged = (s_rot == 0);
+    // Converged after a sweep without rotations, or after one whose every rotation had
+    // |gamma| <= 2^-30 sqrt(alpha beta): Jacobi converges quadratically, so the next sweep's
+    // off-diagonal terms would be ~2^-60 relative, below the tolerance c 2^-53, and rotate nothing
+    // that matters.  Every CTA holds the same totals, so all take the same decision.
+    converged = (s_rot == 0) || (s_big == 0);
     __syncthreads();
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_big = 0;
+    }
     __syncthreads();
   }
   if (!converged && rank == 0 && tid == 0) set_status(&a.hdr->status, RRF_NOT_CONVERGED);

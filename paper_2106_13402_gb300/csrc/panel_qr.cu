@@ -81,23 +81,46 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Partial sums of column j over this CTA's rows (local panel Pl, local row l = global row i0 + l):
 // slot j = sum_{i>j} x_i^2, slot k>j = sum_{i>=j} x_i P(i,k).  Written to out[k * nb].
+// Staged panels (odd column stride in shared memory): tps = NT / (w - j) threads per slot (a power of
+// two) split the rows and combine by shuffles, so FP64 work is one FMA per element plus log2(tps) adds
+// per slot -- on this GPU's narrow FP64 pipe a per-slot warp reduction would cost more than the dot
+// product.  Unstaged panels (rows in global memory): a warp per slot, lanes over rows (coalesced).
 __device__ void column_partials(const PanelArgs& a, int j, const double* Pl, int64_t ldl, int64_t i0, int64_t nloc,
                                 double* xs, double* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t l = tid; l < nloc; l += NT) xs[l] = (i0 + l >= j) ? Pl[l + (int64_t)j * ldl] : 0.0;
   __syncthreads();
   const int64_t lb = (j > i0) ? (j - i0) : 0;  // first local row with i >= j
-  for (int k = j + warp; k < a.w; k += NT / 32) {
+  if (a.staged) {
+    const int slots = a.w - j;
+    int tps = 1;
+    while (tps * 2 * slots <= NT && tps < 32) tps *= 2;
+    const int k = j + tid / tps, sub = tid % tps;
     double acc = 0.0;
-    if (k == j) {
-      for (int64_t l = lb + lane; l < nloc; l += 32)
-        if (i0 + l > j) acc = fma(xs[l], xs[l], acc);
-    } else {
+    if (k < a.w) {
       const double* pk = Pl + (int64_t)k * ldl;
-      for (int64_t l = lb + lane; l < nloc; l += 32) acc = fma(xs[l], pk[l], acc);
+      if (k == j) {
+        for (int64_t l = lb + sub; l < nloc; l += tps)
+          if (i0 + l > j) acc = fma(xs[l], xs[l], acc);
+      } else {
+        for (int64_t l = lb + sub; l < nloc; l += tps) acc = fma(xs[l], pk[l], acc);
+      }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) out[(int64_t)k * a.nb] = acc;
+    for (int o = tps / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (k < a.w && sub == 0) out[(int64_t)k * a.nb] = acc;
+  } else {
+    for (int k = j + warp; k < a.w; k += NT / 32) {
+      double acc = 0.0;
+      if (k == j) {
+        for (int64_t l = lb + lane; l < nloc; l += 32)
+          if (i0 + l > j) acc = fma(xs[l], xs[l], acc);
+      } else {
+        const double* pk = Pl + (int64_t)k * ldl;
+        for (int64_t l = lb + lane; l < nloc; l += 32) acc = fma(xs[l], pk[l], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) out[(int64_t)k * a.nb] = acc;
+    }
   }
   __syncthreads();
 }
@@ -120,7 +143,7 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
   int64_t ldl = a.ldp;
   if (a.staged) {
     Pl = smem + 2 * a.rows_per;
-    ldl = a.rows_per;
+    ldl = a.rows_per | 1;  // odd stride: a thread per column reads distinct banks
     for (int k = warp; k < w; k += NT / 32)
       for (int64_t l = lane; l < nloc; l += 32) Pl[l + k * ldl] = a.P[(i0 + l) + (int64_t)k * a.ldp];
     __syncthreads();
@@ -315,7 +338,7 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   a.rows_per = (r + nb - 1) / nb;
   constexpr size_t kSmemCap = 200 * 1024;
   size_t dyn = (size_t)2 * a.rows_per * sizeof(double);
-  const size_t staged_bytes = dyn + (size_t)a.rows_per * w * sizeof(double);
+  const size_t staged_bytes = dyn + (size_t)(a.rows_per | 1) * w * sizeof(double);
   a.staged = staged_bytes <= kSmemCap ? 1 : 0;
   if (a.staged) dyn = staged_bytes;
   static bool attr_set = false;
