@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "rrf_internal.cuh"
 
@@ -28,6 +29,12 @@ namespace {
 constexpr int NT = 256;
 constexpr int kMaxC = 256;
 constexpr int kMaxSweeps = 40;
+// FP32 pre-pass: one CTA for c <= kPreMaxC, the cluster kernel in FP32 for larger c.
+constexpr int kPreThreads = 1024;
+constexpr int kPreMinC = 32;
+constexpr int kPreMaxC = 128;
+constexpr int kPreSweeps = 10;
+constexpr int kPreLd = kPreMaxC;  // column stride (floats) of the one-CTA pre-pass
 
 struct JacobiArgs {
   int c;
@@ -59,20 +66,24 @@ __device__ __forceinline__ void round_pair(int t, int k, int ne, int& p, int& q)
 }
 
 // CL: cluster size (16 where the GPU schedules such clusters, else 8), given again at launch.
-template <int CL>
+// PRE: FP32 pre-pass for c > 128 -- sweeps on M 2^-e in FP32 (tolerance 2^-16, at most kPreSweeps) and
+// only the accumulated V (as FP64) written to a.Vs; the FP64 sweeps then start from it.
+template <int CL, bool PRE>
 __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ JacobiArgs a) {
+  using T = typename std::conditional<PRE, float, double>::type;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int c = a.c, rp = a.rp, ldl = rp + 1;  // local column stride (padded)
-  double* Ml = smem;                              // [c][ldl]
-  double* Vl = smem + (size_t)c * ldl;            // [c][ldl]
-  double* part = Vl + (size_t)c * ldl;            // [2][CL][kMaxC/2][3]: every CTA's partials, pushed
-  double* nrm = part + 2 * CL * (kMaxC / 2) * 3;  // [kMaxC] partial squared norms
+  T* Ml = smem;                              // [c][ldl]
+  T* Vl = smem + (size_t)c * ldl;            // [c][ldl]
+  T* part = Vl + (size_t)c * ldl;            // [2][CL][kMaxC/2][3]: every CTA's partials, pushed
+  double* nrm = reinterpret_cast<double*>(part + 2 * CL * (kMaxC / 2) * 3);  // [kMaxC] squared norms
   double* vmax = nrm + kMaxC;                     // [kMaxC] partial max |v|
   int* vidx = reinterpret_cast<int*>(vmax + kMaxC);  // [kMaxC] row of the max
   __shared__ int s_rot, s_big;
-  __shared__ double s_cs[kMaxC / 2], s_sn[kMaxC / 2];
+  __shared__ T s_cs[kMaxC / 2], s_sn[kMaxC / 2];
   __shared__ int s_rotf[kMaxC / 2];
   __shared__ double s_sig[kMaxC];
   __shared__ double s_sign[kMaxC];
@@ -81,15 +92,29 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
   const int tid = threadIdx.x;
   const int r0 = rank * rp;
   const int nloc = max(0, min(rp, c - r0));
+  // The FP32 pre-pass scales M by 2^-e (max |M| < 2^e, the same e in every CTA: each reads all of M).
+  int ex = 0;
+  if (PRE) {
+    __shared__ double s_mx[NT / 32];
+    double mx = 0.0;
+    for (int idx = tid; idx < c * c; idx += NT) mx = fmax(mx, fabs(a.M[(idx % c) + (int64_t)(idx / c) * a.ldm]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, s_mx[w]);
+    if (mx > 0.0) frexp(mx, &ex);
+  }
   // Load my rows of M; V starts as V0 (or the identity).
   for (int idx = tid; idx < c * rp; idx += NT) {
     const int col = idx / rp, i = idx % rp;
     const int gi = r0 + i;
-    Ml[col * ldl + i] = (i < nloc) ? a.M[gi + (int64_t)col * a.ldm] : 0.0;
+    const double mv = (i < nloc) ? a.M[gi + (int64_t)col * a.ldm] : 0.0;
+    Ml[col * ldl + i] = PRE ? (T)ldexp(mv, -ex) : (T)mv;
     if (a.V0 != nullptr)
-      Vl[col * ldl + i] = (i < nloc) ? a.V0[gi + (int64_t)col * a.ldv0] : 0.0;
+      Vl[col * ldl + i] = (i < nloc) ? (T)a.V0[gi + (int64_t)col * a.ldv0] : (T)0;
     else
-      Vl[col * ldl + i] = (i < nloc && gi == col) ? 1.0 : 0.0;
+      Vl[col * ldl + i] = (i < nloc && gi == col) ? (T)1 : (T)0;
   }
   if (tid == 0) {
     s_rot = 0;
@@ -109,18 +134,19 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
   int par = 0;
   int sweep = 0;
   bool converged = false;
-  for (sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+  const int max_sweeps = PRE ? kPreSweeps : kMaxSweeps;
+  for (sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
     for (int t = 0; t < rounds; ++t) {
       int p = 0, q = 0;
       if (active) round_pair(t, grp, ne, p, q);
       const bool real = active && q < c;
       // (1) partial alpha, beta, gamma over my rows.
-      double al = 0.0, be = 0.0, ga = 0.0;
+      T al = 0, be = 0, ga = 0;
       if (real) {
-        const double* mp = Ml + p * ldl;
-        const double* mq = Ml + q * ldl;
+        const T* mp = Ml + p * ldl;
+        const T* mq = Ml + q * ldl;
         for (int i = sub; i < nloc; i += tpp) {
-          const double x = mp[i], y = mq[i];
+          const T x = mp[i], y = mq[i];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga = fma(x, y, ga);
@@ -133,11 +159,11 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
       }
       // (2) push my partials into every CTA's buffer (remote stores do not stall), one cluster
       // barrier, then sum the local copies in rank order: identical totals on every CTA.
-      double* slot = part + ((size_t)(par * CL + rank) * (kMaxC / 2) + grp) * 3;
+      T* slot = part + ((size_t)(par * CL + rank) * (kMaxC / 2) + grp) * 3;
       if (active && sub == 0) {
 #pragma unroll
         for (int rr = 0; rr < CL; ++rr) {
-          double* dst = cluster.map_shared_rank(slot, rr);
+          T* dst = cluster.map_shared_rank(slot, rr);
           dst[0] = al;
           dst[1] = be;
           dst[2] = ga;
@@ -151,17 +177,27 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
       if (tid < npairs) {
         int gp, gq;
         round_pair(t, tid, ne, gp, gq);
-        double gcs = 1.0, gsn = 0.0;
+        T gcs = 1, gsn = 0;
         int grot = 0;
         if (gq < c) {
-          double A = 0.0, B = 0.0, G = 0.0;
+          T A = 0, B = 0, G = 0;
 #pragma unroll
           for (int rr = 0; rr < CL; ++rr) {
-            const double* rp3 = part + ((size_t)(par * CL + rr) * (kMaxC / 2) + tid) * 3;
+            const T* rp3 = part + ((size_t)(par * CL + rr) * (kMaxC / 2) + tid) * 3;
             A += rp3[0];
             B += rp3[1];
             G += rp3[2];
           }
+          if (PRE) {
+            if (G != 0.f && G * G > 0x1p-32f * (A * B)) {  // tolerance 2^-16, squared
+              const float zeta = __fdividef(B - A, 2.f * G);
+              const float tt = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+              gcs = rsqrtf(fmaf(tt, tt, 1.f));
+              gsn = gcs * tt;
+              grot = 1;
+              s_rot = 1;
+            }
+          } else {
           const double sab = sqrt(A * B);
           if (G != 0.0 && fabs(G) > tol * sab) {
             const double zeta = (B - A) / (2.0 * G);
@@ -172,24 +208,25 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
             s_rot = 1;
             if (fabs(G) > 0x1p-30 * sab) s_big = 1;
           }
+          }
         }
         s_cs[tid] = gcs;
         s_sn[tid] = gsn;
         s_rotf[tid] = grot;
       }
       __syncthreads();
-      const double cs = active ? s_cs[grp] : 1.0, sn = active ? s_sn[grp] : 0.0;
+      const T cs = active ? s_cs[grp] : (T)1, sn = active ? s_sn[grp] : (T)0;
       const int rot = active ? s_rotf[grp] : 0;
       if (real && rot) {
-        double* mp = Ml + p * ldl;
-        double* mq = Ml + q * ldl;
-        double* vp = Vl + p * ldl;
-        double* vq = Vl + q * ldl;
+        T* mp = Ml + p * ldl;
+        T* mq = Ml + q * ldl;
+        T* vp = Vl + p * ldl;
+        T* vq = Vl + q * ldl;
         for (int i = sub; i < nloc; i += tpp) {
-          const double x = mp[i], y = mq[i];
+          const T x = mp[i], y = mq[i];
           mp[i] = cs * x - sn * y;
           mq[i] = sn * x + cs * y;
-          const double u = vp[i], v = vq[i];
+          const T u = vp[i], v = vq[i];
           vp[i] = cs * u - sn * v;
           vq[i] = sn * u + cs * v;
         }
@@ -202,13 +239,22 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
     // |gamma| <= 2^-30 sqrt(alpha beta): Jacobi converges quadratically, so the next sweep's
     // off-diagonal terms would be ~2^-60 relative, below the tolerance c 2^-53, and rotate nothing
     // that matters.  Every CTA holds the same totals, so all take the same decision.
-    converged = (s_rot == 0) || (s_big == 0);
+    converged = (s_rot == 0) || (!PRE && s_big == 0);
     __syncthreads();
     if (tid == 0) {
       s_rot = 0;
       s_big = 0;
     }
     __syncthreads();
+  }
+  if (PRE) {  // the pre-pass hands over V only
+    if (rank == 0 && tid == 0) a.hdr->flags[2] = sweep;  // diagnostics
+    for (int idx = tid; idx < c * nloc; idx += NT) {
+      const int k = idx / nloc, i = idx % nloc;
+      a.Vs[(r0 + i) + (int64_t)k * a.ldv] = (double)Vl[k * ldl + i];
+    }
+    cluster.sync();
+    return;
   }
   if (!converged && rank == 0 && tid == 0) set_status(&a.hdr->status, RRF_NOT_CONVERGED);
   if (rank == 0 && tid == 0) a.hdr->flags[1] = sweep;  // diagnostics: sweeps of the last SVD
@@ -281,11 +327,6 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
 // with zeros), until a sweep without rotations at tolerance 2^-16 or kPreSweeps sweeps (a looser tolerance
 // costs FP64 sweeps when singular values cluster, a tighter one meets FP32 rounding).  Only the accumulated rotation
 // V32 leaves the kernel: it is a preconditioner, orthonormalized in FP64 afterwards.
-constexpr int kPreThreads = 1024;
-constexpr int kPreMinC = 32;
-constexpr int kPreMaxC = 128;
-constexpr int kPreSweeps = 10;
-constexpr int kPreLd = kPreMaxC;  // column stride (floats)
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -427,10 +468,22 @@ __global__ void __launch_bounds__(NT) complete_kernel(int c, double* Us, int64_t
   if (tid == 0) hdr->flags[0] = 0;
 }
 
-size_t jacobi_smem(int c, int cl) {
+size_t jacobi_smem(int c, int cl, bool pre) {
   const int rp = (c + cl - 1) / cl;
-  return ((size_t)2 * c * (rp + 1) + 2 * cl * (kMaxC / 2) * 3 + 2 * kMaxC) * sizeof(double) +
-         kMaxC * sizeof(int);
+  const size_t elem = pre ? sizeof(float) : sizeof(double);
+  size_t b = ((size_t)2 * c * (rp + 1) + (size_t)2 * cl * (kMaxC / 2) * 3) * elem;
+  b = (b + 15) / 16 * 16;
+  return b + 2 * kMaxC * sizeof(double) + kMaxC * sizeof(int);
+}
+
+template <int CL, bool PRE>
+cudaError_t set_jacobi_attrs() {
+  if (CL > 8) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<CL, PRE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(jacobi_kernel<CL, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)jacobi_smem(kMaxC, CL, PRE));
 }
 
 // 16-CTA clusters are not portable: use them when the device accepts the attribute and can schedule one.
@@ -439,9 +492,7 @@ int jacobi_cluster_size() {
   static std::once_flag once;
   std::call_once(once, [] {
     cl = 8;
-    if (cudaFuncSetAttribute(jacobi_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(jacobi_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)jacobi_smem(kMaxC, 16)) != cudaSuccess) {
+    if (set_jacobi_attrs<16, false>() != cudaSuccess || set_jacobi_attrs<16, true>() != cudaSuccess) {
       cudaGetLastError();
       return;
     }
@@ -453,22 +504,21 @@ int jacobi_cluster_size() {
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = jacobi_smem(kMaxC, 16);
+    cfg.dynamicSmemBytes = jacobi_smem(kMaxC, 16, false);
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, jacobi_kernel<16>, &cfg) == cudaSuccess && n > 0) cl = 16;
+    if (cudaOccupancyMaxActiveClusters(&n, jacobi_kernel<16, false>, &cfg) == cudaSuccess && n > 0) cl = 16;
     cudaGetLastError();
   });
   return cl;
 }
 
-template <int CL>
+template <int CL, bool PRE>
 cudaError_t launch_jacobi(const JacobiArgs& a, int c, cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)jacobi_smem(kMaxC, CL));
+    cudaError_t e = set_jacobi_attrs<CL, PRE>();
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -480,17 +530,17 @@ cudaError_t launch_jacobi(const JacobiArgs& a, int c, cudaStream_t stream) {
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = jacobi_smem(c, CL);
+  cfg.dynamicSmemBytes = jacobi_smem(c, CL, PRE);
   cfg.stream = stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_kernel<CL>, a);
+  return cudaLaunchKernelEx(&cfg, jacobi_kernel<CL, PRE>, a);
 }
 
 }  // namespace
 
 size_t jacobi_scratch_bytes(int64_t c) {
-  if (c < kPreMinC || c > kPreMaxC) return 0;
+  if (c < kPreMinC || c > kMaxC) return 0;
   GemmDesc g;
   g.M = c; g.N = c; g.K = c;
   return align_up((size_t)3 * c * c * sizeof(double), 256) + gemm_scratch_bytes(&g, 1);
@@ -535,10 +585,20 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
       if (e != cudaSuccess) return e;
       attr_pre = true;
     }
-    jacobi_f32_prepass_kernel<<<1, kPreThreads, 2 * c * kPreLd * sizeof(float), stream>>>((int)c, M, ldm, X, c,
-                                                                                    &hdr->flags[2]);
+    if (c <= kPreMaxC) {
+      jacobi_f32_prepass_kernel<<<1, kPreThreads, 2 * c * kPreLd * sizeof(float), stream>>>((int)c, M, ldm, X, c,
+                                                                                      &hdr->flags[2]);
+      e = cudaGetLastError();
+    } else {
+      JacobiArgs pa = a;
+      pa.Vs = X;
+      pa.ldv = c;
+      pa.V0 = nullptr;
+      e = (cl == 16) ? launch_jacobi<16, true>(pa, (int)c, stream) : launch_jacobi<8, true>(pa, (int)c, stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
     count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     for (int it = 0; it < 2; ++it) {
       if ((e = fill_identity(c, c, E, c, stream)) != cudaSuccess) return e;
       GemmDesc g1;  // E = I - X^T X
@@ -571,7 +631,7 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   }
   e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  e = (cl == 16) ? launch_jacobi<16>(a, (int)c, stream) : launch_jacobi<8>(a, (int)c, stream);
+  e = (cl == 16) ? launch_jacobi<16, false>(a, (int)c, stream) : launch_jacobi<8, false>(a, (int)c, stream);
   count_launch();
   if (e != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
