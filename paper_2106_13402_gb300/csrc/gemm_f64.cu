@@ -149,8 +149,8 @@ __global__ void gemm_reduce_kernel(const __grid_constant__ Batch batch) {
 
 int plan_splits(const GemmDesc& d, int sms) {
   const int64_t tiles = ((d.M + BM - 1) / BM) * ((d.N + BN - 1) / BN);
-  if (tiles >= 4LL * sms || d.K < 512) return 1;
-  const int max_s = (int)std::min<int64_t>(32, d.K / 256);
+  if (tiles >= 4LL * sms || d.K < 64) return 1;
+  const int max_s = (int)std::min<int64_t>(32, d.K / 32);
   int best = 1;
   double best_eff = 0.0;
   for (int s = 1; s <= max_s; ++s) {
