@@ -27,6 +27,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "factorizations/s (randUTV + powerURV, FP64, 8192^2, b=128, q=1)"
 WORKLOAD = "randUTV_basic + powerURV on 8192x8192 A = Q1 diag(s) Q2^T, s_j = 10^(-8j/n) (j < n/2) then 1e-4"
+# DRAM bytes (read + write) of one ozaki_gemm_kernel launch of the --workload gemm case, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on this command with the kernel as it is now; set it to
+# None whenever that kernel changes.
+GEMM_4096_DRAM_BYTES = 2.4968e9 + 0.1329e9
 # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (measured 1.19 TFLOP/s at 1995 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -49,9 +53,10 @@ def parse():
                    help="FP64 products: library default, DFMA only, or emulated on the BF16 tensor cores")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 (DFMA) comparison run")
     p.add_argument("--no-per-method", action="store_true", help="skip the per-method timing runs (profiling)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "gemm"],
                    help="c2: FP64 randUTV + powerURV 8192^2 (default); c3: BF16-sketch randUTV 16384^2, b=256, q=2; "
-                        "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128")
+                        "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128; "
+                        "gemm: the dominant kernel alone (FP64 GEMM 4096^3 emulated on the tensor cores)")
     return p.parse_args()
 
 
@@ -584,6 +589,58 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """The emulated FP64 GEMM alone, C = A B with A, B 4096 x 4096 Gaussian (through rrf_gemm_emulated)."""
+    torch, dev = _setup_single_gpu(args)
+    from paper_2106_13402_gb300 import rrf
+    L = rrf.lib()
+    m = n = k = 4096
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    A = rrf.as_fortran(torch.randn(m, k, dtype=torch.float64, device=dev, generator=g))
+    B = rrf.as_fortran(torch.randn(k, n, dtype=torch.float64, device=dev, generator=g))
+    C = rrf.fortran_empty(m, n, dev)
+    ws = rrf.workspace(L.rrf_gemm_emulated_workspace(m, n, k), dev)
+
+    def call():
+        st = L.rrf_gemm_emulated(b"N", b"N", m, n, k, 1.0, rrf._vp(A.data_ptr()), rrf._ld(A), rrf._vp(B.data_ptr()),
+                                 rrf._ld(B), 0.0, rrf._vp(C.data_ptr()), rrf._ld(C), rrf._vp(ws.data_ptr()), ws.numel(),
+                                 rrf._stream(None))
+        if st != 0:
+            raise RuntimeError(f"rrf_gemm_emulated: status {st}")
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    rrf.gemm_profile_begin(1000)
+    ms = _timed(torch, call, args.steps)
+    rrf.gemm_profile_end()
+    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    clocks = sampler.stop()
+    if L.rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None)) != 0:
+        raise RuntimeError("device status")
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["bf16_tflops"])  # a kernel timed alone: the burst figure
+    ach = emu_tflops / (emu_ms / 1e3) / 1e12
+    fl = 2.0 * m * n * k
+    line = {
+        "metric": "TFLOP/s (FP64 GEMM 4096^3, emulated on the BF16 tensor cores)", "value": round(fl / (ms / 1e3) / 1e12, 3),
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (bf16 digit products, int64 accumulation)",
+        "data": "synthetic", "config": {"workload": "C = A B, A and B 4096 x 4096 N(0,1) FP64", "l2": "inputs 256 MB, larger than L2"},
+        "clocks": clocks, "gpu_launches": None,
+        "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": GEMM_4096_DRAM_BYTES,
+                     "traffic_unit": "bytes per launch (dram read + write, ncu)",
+                     "algorithmic_bytes": 2 * 7 * m * k * 2 + 8 * m * n,
+                     "peak_source": f"{peak_src} bf16_tflops (burst)", "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),
+                     "share_of_step": round(emu_ms / (ms * args.steps), 4)},
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -592,6 +649,8 @@ def main():
         run_c3_c5(args)
     elif args.workload == "c4":
         run_c4(args)
+    elif args.workload == "gemm":
+        run_gemm(args)
     else:
         run_ours(args)
 
