@@ -127,6 +127,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def step_flops(n, b, q):
     from paper_2106_13402_gb300 import testmats
     return testmats.flops_randutv(n, n, b, q) + testmats.flops_powerurv(n, n, q)
@@ -237,14 +252,10 @@ def run_ours(args):
     clocks = sampler.stop()
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     flops = (testmats.flops_randutv(n, n, b, q) if "randutv" in methods else 0.0) + \
         (testmats.flops_powerurv(n, n, q) if "powerurv" in methods else 0.0)
-    value = world * len(methods) / (ms / 1e3)
+    value = replica_rate(len(methods), world, ms)
 
     # Per-method device times (one more run each, outside the timed region).
     per = {}
@@ -299,12 +310,8 @@ def run_ours(args):
         for _ in range(args.steps):
             rrf.randutv_host(Ah, b, q, 17, opts=opts, out=hout["randutv"])
             rrf.powerurv_host(Ah, b, q, 17, opts=opts, out=hout["powerurv"])
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": round(world * 2.0 / e2e_s, 5), "unit": "factorizations/s",
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+        e2e = {"value": round(replica_rate(2, world, e2e_s * 1e3), 5), "unit": "factorizations/s",
                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 2 * 3 * 8 * n * n,
                "s_per_step": round(e2e_s, 3)}
 
