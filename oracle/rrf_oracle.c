@@ -501,6 +501,196 @@ int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, i
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * randUTV_boosted (Algorithm 2): randUTV with p oversampled columns whose extra samples are carried
+ * from one step to the next.  Step 1 samples Y = (T^T T)^q T^T G with G of b + p columns; later steps
+ * draw b fresh columns, apply (T22^T T22)^(q-1) T22^T, take X = T22 Y1, remove from X its component
+ * along the recycled directions, orthonormalize, and apply T22^T once more to both blocks.  The left
+ * singular vectors W_Y of the c x (b+p) sample (tall-thin SVD: HQR, then the SVD of the square R)
+ * give V_i = HQR_full(W_Y(:, 1:b)), and W_next = V_i(:, b+1:c)^T W_Y(:, b+1:b+p) carries the rest.
+ * Reading: W_next lives in the column (right-singular) space of the next T22, while X lives in its row
+ * space; the printed lines use W_next where a row-space block is needed, which agrees in shape only
+ * for m = n.  Here the recycled block enters the row space as Z = orth(T22 W_next), so the last
+ * application of T22^T scales fresh and recycled samples alike: X <- X - Z Z^T X, Q = orth(X),
+ * Y = T22^T [Q, Z].  With p = 0 the sampled subspace is that of randUTV_basic for the same q >= 1.
+ * ------------------------------------------------------------------------------------------- */
+/* Orthonormal basis (thin Q, rows x k) of the columns of X (rows x k, k <= rows), via HQR. */
+static void thin_q(int64_t rows, int64_t k, const double* X, int64_t ldx, double* Q, int64_t ldq) {
+  if (k <= 0) return;
+  double* P = (double*)malloc(sizeof(double) * (size_t)rows * (size_t)k);
+  double* tau = (double*)malloc(sizeof(double) * (size_t)k);
+  copy_block(rows, k, X, ldx, P, rows);
+  orc_hqr(rows, k, P, rows, tau);
+  orc_form_q(rows, k, k, P, rows, tau, Q, ldq);
+  free(P);
+  free(tau);
+}
+
+int orc_randutv_boosted(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, int64_t p,
+                        uint64_t seed, double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                        int max_steps) {
+  if (m < n || n < 1 || b < 1 || q < 0 || p < 0 || lda < m || ldu < m || ldt < m || ldv < n) return 1;
+  int status = 0;
+  copy_block(m, n, A, lda, T, ldt);
+  for (int64_t j = 0; j < m; ++j)
+    for (int64_t i = 0; i < m; ++i) U[IDX(i, j, ldu)] = (i == j) ? 1.0 : 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) V[IDX(i, j, ldv)] = (i == j) ? 1.0 : 0.0;
+
+  const int64_t steps_m = (m + b - 1) / b, steps_n = (n + b - 1) / b;
+  const int64_t s = steps_m < steps_n ? steps_m : steps_n;
+  const int64_t bp = b + p;
+  double* G = (double*)malloc(sizeof(double) * (size_t)m * (size_t)bp);
+  double* Y = (double*)malloc(sizeof(double) * (size_t)n * (size_t)bp);
+  double* Z = (double*)malloc(sizeof(double) * (size_t)m * (size_t)bp);
+  double* X = (double*)malloc(sizeof(double) * (size_t)m * (size_t)bp);
+  double* Qx = (double*)malloc(sizeof(double) * (size_t)m * (size_t)bp);
+  double* Wn = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(p > 0 ? p : 1));
+  double* Wy = (double*)malloc(sizeof(double) * (size_t)n * (size_t)bp);
+  double* Py = (double*)malloc(sizeof(double) * (size_t)n * (size_t)bp);
+  double* ty = (double*)malloc(sizeof(double) * (size_t)bp);
+  double* Ry = (double*)malloc(sizeof(double) * (size_t)bp * (size_t)bp);
+  double* Uy = (double*)malloc(sizeof(double) * (size_t)bp * (size_t)bp);
+  double* Vy = (double*)malloc(sizeof(double) * (size_t)bp * (size_t)bp);
+  double* sy = (double*)malloc(sizeof(double) * (size_t)bp);
+  double* tauv = (double*)malloc(sizeof(double) * (size_t)b);
+  double* tauu = (double*)malloc(sizeof(double) * (size_t)b);
+  double* P = (double*)malloc(sizeof(double) * (size_t)m * (size_t)b);
+  double* Rs = (double*)malloc(sizeof(double) * (size_t)b * (size_t)b);
+  double* Usm = (double*)malloc(sizeof(double) * (size_t)b * (size_t)b);
+  double* Vsm = (double*)malloc(sizeof(double) * (size_t)b * (size_t)b);
+  double* sig = (double*)malloc(sizeof(double) * (size_t)b);
+  int have_next = 0;
+
+  for (int64_t i = 1; i <= s; ++i) {
+    if (max_steps > 0 && i > max_steps) break;
+    const int64_t o = b * (i - 1);
+    const int64_t r = m - o, c = n - o;
+    double* T22 = T + IDX(o, o, ldt);
+    if (b * i < m && b * i < n) {
+      /* the sample has k columns: b + p, or fewer when the trailing block is narrower */
+      const int64_t pk = (bp <= c) ? p : (c - b);
+      const int64_t k = b + pk;
+      if (i == 1 || !have_next || pk == 0) {
+        /* G = randn(r, k); Y = T22^T G; Y = T22^T (T22 Y) q times (at step 1; later steps without a
+         * recycled block fall back to this form with k = b). */
+        const int64_t kk = (i == 1) ? k : b;
+        orc_randn(r, kk, G, r, seed, (uint32_t)i, 1u);
+        orc_gemm('T', 'N', c, kk, r, 1.0, T22, ldt, G, r, 0.0, Y, c);
+        for (int j = 0; j < q; ++j) {
+          orc_gemm('N', 'N', r, kk, c, 1.0, T22, ldt, Y, c, 0.0, Z, r);
+          orc_gemm('T', 'N', c, kk, r, 1.0, T22, ldt, Z, r, 0.0, Y, c);
+        }
+        if (kk < k) { /* no recycled block available: sample the extra columns fresh as well */
+          orc_randn(r, k, G, r, seed, (uint32_t)i, 3u);
+          orc_gemm('T', 'N', c, k - kk, r, 1.0, T22, ldt, G + IDX(0, kk, r), r, 0.0, Y + IDX(0, kk, c), c);
+          for (int j = 0; j < q; ++j) {
+            orc_gemm('N', 'N', r, k - kk, c, 1.0, T22, ldt, Y + IDX(0, kk, c), c, 0.0, Z, r);
+            orc_gemm('T', 'N', c, k - kk, r, 1.0, T22, ldt, Z, r, 0.0, Y + IDX(0, kk, c), c);
+          }
+        }
+      } else {
+        /* G = randn(r, b); Y1 = T22^T G; Y1 = T22^T (T22 Y1) q - 1 times; X = T22 Y1. */
+        orc_randn(r, b, G, r, seed, (uint32_t)i, 1u);
+        orc_gemm('T', 'N', c, b, r, 1.0, T22, ldt, G, r, 0.0, Y, c);
+        for (int j = 0; j + 1 < q; ++j) {
+          orc_gemm('N', 'N', r, b, c, 1.0, T22, ldt, Y, c, 0.0, Z, r);
+          orc_gemm('T', 'N', c, b, r, 1.0, T22, ldt, Z, r, 0.0, Y, c);
+        }
+        orc_gemm('N', 'N', r, b, c, 1.0, T22, ldt, Y, c, 0.0, X, r);
+        /* Z = orth(T22 W_next) (r x pk); X <- X - Z (Z^T X); Q = orth(X); Y = T22^T [Q, Z]. */
+        orc_gemm('N', 'N', r, pk, c, 1.0, T22, ldt, Wn, c, 0.0, Qx, r);
+        thin_q(r, pk, Qx, r, Z, r);
+        double* ZtX = (double*)malloc(sizeof(double) * (size_t)pk * (size_t)b);
+        orc_gemm('T', 'N', pk, b, r, 1.0, Z, r, X, r, 0.0, ZtX, pk);
+        orc_gemm('N', 'N', r, b, pk, -1.0, Z, r, ZtX, pk, 1.0, X, r);
+        free(ZtX);
+        thin_q(r, b, X, r, Qx, r);
+        copy_block(r, pk, Z, r, Qx + IDX(0, b, r), r);
+        orc_gemm('T', 'N', c, k, r, 1.0, T22, ldt, Qx, r, 0.0, Y, c);
+      }
+      /* W_Y = left singular vectors of Y (c x k): HQR_full(Y) = Q_Y [R; 0], svd(R) = U_R D V_R^T,
+       * W_Y(:, 1:k) = Q_Y(:, 1:k) U_R. */
+      copy_block(c, k, Y, c, Py, c);
+      orc_hqr(c, k, Py, c, ty);
+      for (int64_t jj = 0; jj < k; ++jj)
+        for (int64_t ii = 0; ii < k; ++ii) Ry[IDX(ii, jj, k)] = (ii <= jj) ? Py[IDX(ii, jj, c)] : 0.0;
+      int st = orc_jacobi_svd(k, k, Ry, k, Uy, k, sy, Vy, k, NULL);
+      if (st != 0) status = st;
+      for (int64_t jj = 0; jj < k; ++jj)
+        for (int64_t ii = 0; ii < c; ++ii) Wy[IDX(ii, jj, c)] = (ii < k) ? Uy[IDX(ii, jj, k)] : 0.0;
+      orc_apply_q('L', 'N', c, k, k, Py, c, ty, Wy, c);
+      /* [V_i, ~] = HQR_full(W_Y(:, 1:b)); T(:, J2 u J3) V_i; V(:, J2 u J3) V_i. */
+      double* Yv = (double*)malloc(sizeof(double) * (size_t)c * (size_t)b);
+      copy_block(c, b, Wy, c, Yv, c);
+      orc_hqr(c, b, Yv, c, tauv);
+      orc_apply_q('R', 'N', m, c, b, Yv, c, tauv, T + IDX(0, o, ldt), ldt);
+      orc_apply_q('R', 'N', n, c, b, Yv, c, tauv, V + IDX(0, o, ldv), ldv);
+      /* W_next = V_i(:, b+1:c)^T W_Y(:, b+1:b+pk): rows b..c-1 of V_i^T W_Y(:, b:k). */
+      have_next = 0;
+      if (pk > 0) {
+        orc_apply_q('L', 'T', c, pk, b, Yv, c, tauv, Wy + IDX(0, b, c), c);
+        for (int64_t jj = 0; jj < pk; ++jj)
+          for (int64_t ii = 0; ii < c - b; ++ii) Wn[IDX(ii, jj, c - b)] = Wy[IDX(b + ii, b + jj, c)];
+        have_next = 1;
+      }
+      free(Yv);
+      /* The rest of the step is that of randUTV_basic. */
+      copy_block(r, b, T22, ldt, P, r);
+      orc_hqr(r, b, P, r, tauu);
+      orc_apply_q('R', 'N', m, r, b, P, r, tauu, U + IDX(0, o, ldu), ldu);
+      orc_apply_q('L', 'T', r, c - b, b, P, r, tauu, T + IDX(o, o + b, ldt), ldt);
+      for (int64_t jj = 0; jj < b; ++jj)
+        for (int64_t ii = 0; ii < b; ++ii) Rs[IDX(ii, jj, b)] = (ii <= jj) ? P[IDX(ii, jj, r)] : 0.0;
+      for (int64_t jj = 0; jj < b; ++jj)
+        for (int64_t ii = b; ii < r; ++ii) T[IDX(o + ii, o + jj, ldt)] = 0.0;
+      st = orc_jacobi_svd(b, b, Rs, b, Usm, b, sig, Vsm, b, NULL);
+      if (st != 0) status = st;
+      right_mul_small(m, b, U + IDX(0, o, ldu), ldu, Usm, b);
+      right_mul_small(n, b, V + IDX(0, o, ldv), ldv, Vsm, b);
+      for (int64_t jj = 0; jj < b; ++jj)
+        for (int64_t ii = 0; ii < b; ++ii) T[IDX(o + ii, o + jj, ldt)] = (ii == jj) ? sig[ii] : 0.0;
+      left_mul_small_t(b, c - b, T + IDX(o, o + b, ldt), ldt, Usm, b);
+      right_mul_small(o, b, T + IDX(0, o, ldt), ldt, Vsm, b);
+    } else {
+      /* Final block, as in randUTV_basic. */
+      double* Uf = (double*)malloc(sizeof(double) * (size_t)r * (size_t)c);
+      double* Vf = (double*)malloc(sizeof(double) * (size_t)c * (size_t)c);
+      double* sf = (double*)malloc(sizeof(double) * (size_t)c);
+      int st;
+      if (r > c) {
+        double* Pf = (double*)malloc(sizeof(double) * (size_t)r * (size_t)c);
+        double* tf = (double*)malloc(sizeof(double) * (size_t)c);
+        double* Rf = (double*)malloc(sizeof(double) * (size_t)c * (size_t)c);
+        copy_block(r, c, T22, ldt, Pf, r);
+        orc_hqr(r, c, Pf, r, tf);
+        for (int64_t jj = 0; jj < c; ++jj)
+          for (int64_t ii = 0; ii < c; ++ii) Rf[IDX(ii, jj, c)] = (ii <= jj) ? Pf[IDX(ii, jj, r)] : 0.0;
+        st = orc_jacobi_svd(c, c, Rf, c, Uf, c, sf, Vf, c, NULL);
+        orc_apply_q('R', 'N', m, r, c, Pf, r, tf, U + IDX(0, o, ldu), ldu);
+        right_mul_small(m, c, U + IDX(0, o, ldu), ldu, Uf, c);
+        free(Pf);
+        free(tf);
+        free(Rf);
+      } else {
+        st = orc_jacobi_svd(r, c, T22, ldt, Uf, r, sf, Vf, c, NULL);
+        right_mul_small(m, c, U + IDX(0, o, ldu), ldu, Uf, r);
+      }
+      if (st != 0) status = st;
+      right_mul_small(n, c, V + IDX(0, o, ldv), ldv, Vf, c);
+      for (int64_t jj = 0; jj < c; ++jj)
+        for (int64_t ii = 0; ii < r; ++ii) T[IDX(o + ii, o + jj, ldt)] = (ii == jj) ? sf[ii] : 0.0;
+      right_mul_small(o, c, T + IDX(0, o, ldt), ldt, Vf, c);
+      free(Uf);
+      free(Vf);
+      free(sf);
+    }
+  }
+  free(G); free(Y); free(Z); free(X); free(Qx); free(Wn); free(Wy); free(Py); free(ty); free(Ry);
+  free(Uy); free(Vy); free(sy); free(tauv); free(tauu); free(P); free(Rs); free(Usm); free(Vsm); free(sig);
+  return status;
+}
+
+/* ---------------------------------------------------------------------------------------------
  * powerURV (Algorithm 1): V = randn(n, n); q times { Yh = A V; Vh = HQR_thin(Yh); Y = A^T Vh;
  * V = HQR_thin(Y) }; Ah = A V; [U, R] = HQR_full(Ah).  For q = 0, V = Q of HQR_full(G) (RURV, Sec. 3.1).
  * ------------------------------------------------------------------------------------------- */

@@ -62,6 +62,11 @@ int orc_jacobi_svd(int64_t r, int64_t c, const double* M, int64_t ldm, double* U
 int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
                 double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps);
 
+/* randUTV_boosted (Algorithm 2) with oversampling p and recycled samples; p = 0 samples the subspace of
+ * randUTV_basic (q >= 1).  Same outputs and conventions as orc_randutv. */
+int orc_randutv_boosted(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, int64_t p,
+                        uint64_t seed, double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                        int max_steps);
 /* powerURV (Algorithm 1).  U (m x m), R (m x n, upper trapezoidal), V (n x n).  The Gaussian is
  * orc_randn(n, n, ..., seed, step = 0, tag = 2).  For q = 0, V is the Q factor of HQR_full(G) (RURV). */
 int orc_powerurv(int64_t m, int64_t n, const double* A, int64_t lda, int q, uint64_t seed, double* U,

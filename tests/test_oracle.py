@@ -431,3 +431,90 @@ def test_mlp_zero_network_closed_form():
     expect = np.array([0.25 - np.mean(y == k) for k in range(4)])
     np.testing.assert_allclose(g[-4:], expect, atol=1e-15)
     assert np.all(g[:-4] == 0.0)
+
+
+# ----------------------------------------------------------------------- randUTV_boosted --
+@pytest.mark.parametrize("m,n,b,q,p", [(96, 96, 16, 0, 16), (96, 96, 16, 1, 8), (100, 90, 16, 2, 16),
+                                       (70, 70, 16, 1, 40), (64, 50, 8, 2, 0)])
+def test_boosted_factorization_is_exact(m, n, b, q, p):
+    """Alg. 2 keeps A = U T V^T with U, V orthogonal and the block-diagonal structure of T, for ragged
+    sizes, tall inputs, p from 0 to more than the trailing width."""
+    A, _ = testmats.make_matrix(m, n, "exp8", 3, 4)
+    U, T, V, st = oracle.randutv_boosted(A, b, q, p, seed=13)
+    assert st == 0
+    check_utv(A, U, T, V, b)
+
+
+@pytest.mark.parametrize("m,n,b,q,p", [(8, 8, 3, 1, 2), (8, 6, 2, 2, 2), (7, 7, 2, 1, 5)])
+def test_boosted_tiny_brute_force(m, n, b, q, p):
+    """Every e_k is at least sigma_{k+1} (Eckart-Young) and equals the Eq. (1) error of the rank-k part."""
+    rng = np.random.default_rng(300 + m + n + b + q + p)
+    A = rng.standard_normal((m, n))
+    U, T, V, st = oracle.randutv_boosted(A, b, q, p, seed=17)
+    assert st == 0
+    check_utv(A, U, T, V, b)
+    sv = np.linalg.svd(A, compute_uv=False)
+    for k in range(1, n):
+        e = ek_spectral(T, k)
+        assert abs(e - np.linalg.norm(A - U[:, :k] @ T[:k, :] @ V.T, 2)) <= 1e-12 * sv[0]
+        assert e >= sv[k] * (1 - 1e-12)
+
+
+def test_boosted_step1_equals_oversampled_range():
+    """Step 1 (Sec. 4.2 method b): V(:, :b) spans the top b left singular vectors W_b of
+    Y = (A^T A)^q A^T G with b + p columns, and U(:, :b) spans A W_b, so e_b = ||(I - Q Q^T) A||_2 with
+    Q = orth(A W_b) -- an independent route through numpy from the same Gaussian G."""
+    A, s = testmats.make_matrix(80, 64, "exp100", 1, 2)
+    A = A * np.exp(-np.arange(64) / 10.0)
+    b, q, p, seed = 8, 1, 8, 23
+    U, T, V, st = oracle.randutv_boosted(A, b, q, p, seed, max_steps=1)
+    G = oracle.randn(80, b + p, seed, 1, 1)
+    Y = A.T @ G
+    for _ in range(q):
+        Y = A.T @ (A @ Y)
+    Wy = np.linalg.svd(Y, full_matrices=False)[0][:, :b]
+    Q, _ = np.linalg.qr(A @ Wy)
+    e_route = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+    assert abs(ek_spectral(T, b) - e_route) <= 1e-10 * e_route
+    np.testing.assert_allclose(V[:, :b] @ V[:, :b].T, Wy @ Wy.T, atol=1e-9)
+
+
+def test_boosted_without_oversampling_matches_basic_first_step():
+    """p = 0: step 1 samples the same subspace as randUTV_basic (same Gaussian), so the first block's
+    singular values and the trailing block's spectrum agree to rounding."""
+    A, _ = testmats.make_matrix(128, 128, "exp100", 1, 2)
+    _, Tb, _, _ = oracle.randutv(A, 16, 1, 7, max_steps=1)
+    _, T0, _, _ = oracle.randutv_boosted(A, 16, 1, 0, 7, max_steps=1)
+    np.testing.assert_allclose(np.diag(T0)[:16], np.diag(Tb)[:16], rtol=1e-12)
+    np.testing.assert_allclose(np.linalg.svd(T0[16:, 16:], compute_uv=False),
+                               np.linalg.svd(Tb[16:, 16:], compute_uv=False), rtol=1e-10, atol=1e-14)
+
+
+def test_boosted_exact_rank():
+    A, _ = testmats.make_matrix(48, 40, "rank", 5, 6, rank=16)
+    U, T, V, st = oracle.randutv_boosted(A, 8, 1, 8, seed=9)
+    check_utv(A, U, T, V, 8)
+    assert ek_spectral(T, 16) <= 1e-13 * np.linalg.norm(A, 2)
+    assert ek_spectral(T, 15) > 1e-3 * np.linalg.norm(A, 2)
+
+
+def test_boosted_partial_steps_keep_factorization():
+    A, _ = testmats.make_matrix(96, 96, "poly", 3, 4)
+    U, T, V, st = oracle.randutv_boosted(A, 16, 1, 16, seed=5, max_steps=2)
+    assert np.linalg.norm(A - U @ T @ V.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.all(T[32:, :32] == 0.0)
+
+
+def test_boosted_reaches_boundary_target_where_basic_does_not():
+    """Sec. 6.2: oversampling removes the error spikes at block boundaries.  On the exp(-j/100) input
+    (512^2, b = 32, q = 2) randUTV_basic stays above 1.1 sigma_{k+1} at boundaries while Alg. 2 with
+    p = b is within it at every one (measured 1.169 vs 1.063)."""
+    A, s = testmats.make_matrix(512, 512, "exp100", 1, 2)
+    b = 32
+    _, Tb, _, _ = oracle.randutv(A, b, 2, 7)
+    _, To, _, _ = oracle.randutv_boosted(A, b, 2, b, 7)
+    rb = [ek_spectral(Tb, k) / s[k] for k in range(b, 512, b)]
+    ro = [ek_spectral(To, k) / s[k] for k in range(b, 512, b)]
+    assert max(rb) > 1.1
+    assert max(ro) <= 1.1
+    assert np.mean(ro) < np.mean(rb)
