@@ -1,0 +1,69 @@
+"""GPU parity at the full 8192^2 size, in the configuration bench.py times (b = 128, q = 1, default GEMM
+routing, the s_j = 10^(-8j/n) / 1e-4 input with its seeds): properties that hold at any size on every
+output, and the first randUTV step -- what the FP64 oracle computes here in seconds -- against the oracle
+on the same Gaussian.
+
+Tolerances are those of the smaller parity cases: residual and orthogonality <= 1e-12, exact zeros below
+the diagonal and off the diagonal of each b x b block; the first block's singular values within 1e-10
+relative (+1e-11 ||A||_2) of the oracle's; ||T(b:, b:)||_F, which later steps only rotate, within 1e-10
+relative of the oracle's after its first step.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2106_13402_gb300 import rrf, testmats
+
+pytestmark = pytest.mark.gpu
+N, B, Q, SEED = 8192, 128, 1, 17
+
+
+@pytest.fixture(scope="module")
+def problem():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    A, s = testmats.make_matrix(N, N, "c2", 11, 12, device="cuda")
+    return A, s
+
+
+def _check_exact(A, U, T, V, b=None):
+    eye = torch.eye(N, dtype=torch.float64, device=A.device)
+    res = float(torch.linalg.norm(A - U @ T @ V.t()) / torch.linalg.norm(A))
+    assert res <= 1e-12, res
+    assert float((U.t() @ U - eye).abs().max()) <= 1e-12
+    assert float((V.t() @ V - eye).abs().max()) <= 1e-12
+    assert bool((torch.tril(T, -1) == 0).all())
+    if b is not None:
+        for o in range(0, N, b):
+            blk = T[o:o + b, o:o + b]
+            assert bool((blk - torch.diag(torch.diagonal(blk)) == 0).all())
+
+
+@pytest.mark.slow
+def test_randutv_8192_exact_and_first_step_matches_oracle(problem):
+    A, s = problem
+    U, T, V = rrf.randutv(A, B, Q, seed=SEED)
+    torch.cuda.synchronize()
+    _check_exact(A, U, T, V, B)
+    d_gpu = torch.diagonal(T)[:B].abs().cpu().numpy()
+    f_gpu = float(torch.linalg.norm(T[B:, B:]))
+    del U, V
+    A_h = A.cpu().numpy()
+    Uo, To, Vo, st = oracle.randutv(A_h, B, Q, SEED, max_steps=1)
+    assert st == 0
+    d_orc = np.abs(np.diag(To))[:B]
+    assert np.all(np.abs(d_gpu - d_orc) <= 1e-10 * d_orc + 1e-11 * float(s[0]))
+    f_orc = float(np.linalg.norm(To[B:, B:]))
+    assert abs(f_gpu - f_orc) <= 1e-10 * f_orc
+
+
+@pytest.mark.slow
+def test_powerurv_8192_exact(problem):
+    A, s = problem
+    U, T, V = rrf.powerurv(A, B, Q, seed=SEED)
+    torch.cuda.synchronize()
+    _check_exact(A, U, T, V)
