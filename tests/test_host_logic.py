@@ -1,0 +1,61 @@
+"""Host-side logic on the CPU: the learned policy's label and decision rules, and the bench's clock record."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2106_13402_gb300 import qpolicy  # noqa: E402
+
+
+def test_acceptable_meets_target_or_stays_near_the_better_fallback():
+    sig = np.array([1.0, 1.0, 1.0])
+    # columns: boundaries; rows: q = 0..3
+    errs = np.array([[1.05, 1.50, 2.00],
+                     [1.04, 1.30, 1.60],
+                     [1.03, 1.20, 1.40],
+                     [1.02, 1.12, 1.20]])
+    ok = qpolicy.acceptable(errs, sig)
+    assert ok[:, 0].all()                                  # every q within 1.1 sigma
+    assert list(ok[:, 1]) == [False, False, False, True]   # none within 1.1; 1.05 x 1.12 = 1.176 admits q = 3 only
+    assert list(ok[:, 2]) == [False, False, False, True]
+    labels = np.argmax(ok, axis=0)
+    assert list(labels) == [0, 3, 3]
+
+
+def test_acceptable_uses_the_better_of_q2_and_q3_as_reference():
+    sig = np.array([0.5])
+    errs = np.array([[1.0], [0.80], [0.70], [0.69]])
+    ok = qpolicy.acceptable(errs, sig)[:, 0]
+    # reference min(0.70, 0.69) = 0.69 -> slack 0.7245: q = 2 and q = 3 qualify, q = 1 does not
+    assert list(ok) == [False, False, True, True]
+
+
+def test_decide_takes_smallest_q_reaching_the_confidence():
+    # softmax probabilities 0.4, 0.35, 0.2, 0.05: argmax would say 0, the 0.8 rule says 2
+    p = np.array([[0.4, 0.35, 0.2, 0.05], [0.9, 0.05, 0.03, 0.02], [0.1, 0.1, 0.1, 0.7]])
+    z = np.log(p)
+    assert list(qpolicy.decide(z)) == [2, 0, 3]
+    assert list(qpolicy.decide(z, confidence=0.5)) == [1, 0, 3]
+
+
+def test_clock_summary_reports_throttle_reasons():
+    lines = [
+        "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1995, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n",
+        "0, 1500, 2070, 1390.0, 0x8, Active, Not Active, Not Active, Active\n",
+        "garbage line\n",
+    ]
+    c = bench.ClockSampler.summarize(lines)
+    assert c["samples"] == 3 and c["sm_mhz"] == 1995 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler.summarize(["x"]) is None
+
+
+def test_measured_peaks_fall_back_when_absent(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
