@@ -1,7 +1,8 @@
 /*
  * rrf_oracle.h -- FP64 CPU oracle for the randomized rank-revealing factorizations of
  * "Efficient algorithms for computing rank-revealing factorizations on a GPU"
- * (randUTV_basic, Algorithm 3 / appendix "randUTV algorithm adapted from ...", and powerURV, Algorithm 1).
+ * (randUTV_basic, Algorithm 3 / appendix "randUTV algorithm adapted from ...", powerURV, Algorithm 1, and
+ * randUTV_boosted, Algorithm 2).
  *
  * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that the CUDA path is checked
  * against.  Only the test suite, the package's smoke check and the CPU-baseline leg of the benchmark

@@ -20,7 +20,7 @@ import time
 
 import numpy as np
 
-from . import rrf, testmats
+from . import rrf
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "qpolicy_fp16.npy")
