@@ -215,9 +215,11 @@ RRF_API rrf_status rrf_panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, do
  * largest-magnitude entry is positive.  Columns with s_k = 0 get u_k by Gram-Schmidt completion.
  * The rotation rule and stopping test are those of Hestenes' method with tolerance c * 2^-53;
  * the column pairs follow a round-robin (tournament) ordering.  Status (converged or not) goes to
- * the workspace status word.  For 32 <= c <= 128 with rrf_jacobi_svd_workspace(c) bytes, FP32 sweeps
+ * the workspace status word.  For 32 <= c <= 256 with rrf_jacobi_svd_workspace(c) bytes, FP32 sweeps
  * first give a starting V (made orthogonal in FP64 by two Newton-Schulz steps) and the FP64 sweeps run
- * on M V from there; a workspace of just the header size runs the FP64 sweeps from V = I. */
+ * on M V from there; the FP64 sweeps also stop after a sweep whose rotations all had
+ * |gamma| <= 2^-30 sqrt(alpha beta).  A workspace of just the header size runs the FP64 sweeps from
+ * V = I. */
 RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
 RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                           double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream);

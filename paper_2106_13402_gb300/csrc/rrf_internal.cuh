@@ -130,7 +130,7 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
 
 // ---- Jacobi SVD (jacobi.cu) -----------------------------------------------------------------------
 // One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.  With scratch of at least
-// jacobi_scratch_bytes(c) (> 0 for 32 <= c <= 128) an FP32 pre-pass supplies the starting V.
+// jacobi_scratch_bytes(c) (> 0 for 32 <= c <= 256) an FP32 pre-pass supplies the starting V.
 size_t jacobi_scratch_bytes(int64_t c);
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch = nullptr,
