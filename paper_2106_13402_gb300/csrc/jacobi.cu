@@ -2,14 +2,18 @@
 // the last block), on one thread-block cluster.
 //
 // FP64 on GB300 runs at ~2 DFMA/clk/SM, so a single SM would need ~10 ms for a 128 x 128 SVD; the
-// cluster spreads the rows of M and of the accumulated V over CL = 16 (or 8) CTAs (distributed shared memory):
+// cluster spreads the rows of M and of the accumulated V over CL CTAs (8, or 16 for c > 128 where the
+// device schedules such clusters; distributed shared memory):
 // each CTA computes its partial column norms / inner products for all pairs of one round, the
 // partials are summed in rank order through DSMEM after one cluster barrier, every CTA derives the
 // identical rotation, and applies it to its own rows.  Pairs follow the round-robin (tournament)
 // ordering, so each round rotates c/2 disjoint pairs at once.  The rotation rule and stopping test
 // are Hestenes': skip when |gamma| <= tol sqrt(alpha beta) (tol = c 2^-53), otherwise
 // zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1+t^2),
-// sn = cs t; stop after a sweep without rotations (cap 40 sweeps -> RRF_NOT_CONVERGED).
+// sn = cs t; stop after a sweep without rotations, or after one whose rotations all had
+// |gamma| <= 2^-30 sqrt(alpha beta) (cap 40 sweeps -> RRF_NOT_CONVERGED).
+// With scratch, an FP32 pre-pass (one CTA for c <= 128, the cluster kernel in FP32 above) gives the
+// starting V, two FP64 Newton-Schulz steps make it orthogonal, and the FP64 sweeps run on M V.
 // Outputs: sigma_k = ||m_k|| sorted descending (ties by index), u_k = m_k / sigma_k, and each pair
 // signed so the largest-magnitude entry of v_k (first on ties) is positive.  A zero sigma_k leaves
 // u_k for the Gram-Schmidt completion kernel.
