@@ -6,12 +6,14 @@
 // known (v^T P(:, k)).  Here the second is avoided: with v = (x - beta e1) / (alpha - beta),
 //     v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta),
 // so one reduction of [sigma^2, x^T P(:, j+1:w)] plus the owner's copy of row j gives every CTA the
-// reflector and all update coefficients.  One grid barrier per column.  Partial sums are added in
-// CTA order, so the result is bitwise deterministic.  Every barrier wait is bounded in time and
-// records RRF_TIMEOUT in the workspace status word instead of hanging.
+// reflector and all update coefficients.  One grid barrier per column.  Partial sums are combined in
+// a fixed order (per slot: every 8th CTA per thread, then a fixed shuffle tree), so the result is
+// bitwise deterministic.  Every barrier wait is bounded in time and records RRF_TIMEOUT in the
+// workspace status word instead of hanging.
 //
-// The compact-WY factor (Schreiber & Van Loan) is built from the Gram matrix S = Y^T Y by the forward
-// recurrence Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j), Tf(j, j) = tau_j.
+// The compact-WY factor (Schreiber & Van Loan) is built from the Gram matrix S = Y^T Y (through the
+// caller's GEMM router when given) by the forward recurrence Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j),
+// Tf(j, j) = tau_j.
 #include <algorithm>
 
 #include "rrf_internal.cuh"

@@ -9,7 +9,9 @@
 //   Jacobi SVD of R -> (Us, D, Vs); U(:, I2) Us, V(:, J2) Vs, Us^T T(I2, J3), T(I1, J2) Vs,
 //   T(I2 u I3, J2) = [D; 0].
 // The last step (J3 empty) takes the SVD of the r x c remainder, through HQR first when r > c.
-// Everything is enqueued on the caller's stream; nothing is allocated.
+// Every product goes through the GEMM router (tensor-core FP64 emulation for large products by
+// default); the BF16 sketch and the learned per-step q are options.  Everything is enqueued on the
+// caller's stream and nothing is allocated; the learned policy synchronizes once per step.
 #include <algorithm>
 #include <vector>
 
