@@ -85,7 +85,12 @@ typedef struct rrf_opts {
   int* q_used_out;   /* optional HOST array [steps]: the q each step used                              */
   float* features_out; /* optional HOST array [steps x 16]: the features of each step (learned policy) */
   int gemm_mode;     /* RRF_GEMM_AUTO (default), RRF_GEMM_NATIVE or RRF_GEMM_EMULATED */
-  int reserved[3];   /* must be zero */
+  int oversample;    /* p >= 0.  p > 0 runs randUTV_boosted (Algorithm 2, Secs. 4.2-4.3) instead of
+                        randUTV_basic: b + p sample columns, V_i from the leading b left singular vectors
+                        of the sample, and the other p carried into the next step (see rrf_randutv).
+                        1 <= b + p <= 256; p > 0 requires the FP64 sketch, reorth = 0 and fixed q
+                        (q_per_block allowed).  0 (default) is randUTV_basic.                       */
+  int reserved[2];   /* must be zero */
 } rrf_opts;
 
 /* ------------------------------------------------------------------------------------------------
@@ -103,6 +108,15 @@ typedef struct rrf_opts {
  *   V, ldv    : output n x n orthogonal, ldv >= n.
  *   seed      : key of the Gaussian stream.
  * Returns RRF_OK once all work is enqueued.
+ *
+ * With opts->oversample = p > 0 the sample of each step is that of randUTV_boosted (Algorithm 2), with
+ * k = b + min(p, c - b) columns.  Step 1: G = randn(r, k) (step 1, tag 1; its first b columns are
+ * randUTV_basic's G), Y = (T22^T T22)^q T22^T G.  Later steps recycle the previous step's p extra
+ * directions W_next (c x p, expressed in the current trailing columns): G = randn(r, b) (tag 1),
+ * Y1 = (T22^T T22)^(q-1) T22^T G, X = T22 Y1, Z = orth(T22 W_next), X <- X - Z (Z^T X), Q = orth(X),
+ * Y = T22^T [Q, Z].  Then W_Y = the left singular vectors of Y (Householder QR of Y, Jacobi SVD of its
+ * k x k R, both FP64), V_i = HQR_full(W_Y(:, 1:b)) and W_next = rows b.. of V_i^T W_Y(:, b+1:k).  The
+ * rest of the step (and the last step) is that of randUTV_basic.
  * ---------------------------------------------------------------------------------------------- */
 RRF_API size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
 RRF_API rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,

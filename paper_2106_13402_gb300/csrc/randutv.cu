@@ -41,16 +41,21 @@ struct RWs {
   // learned q policy: features of the current step, the chosen q
   float* feat = nullptr;
   int* qdev = nullptr;
+  // randUTV_boosted (oversampling p > 0): the k = b + p column sample, its SVD (Q_Y reflectors, R, U_R,
+  // V_R, D), the left singular vectors W_Y, the recycled directions W_next, thin-Q scratch.
+  double *Qk = nullptr, *Xk = nullptr, *Wy = nullptr, *Wn = nullptr, *Yq = nullptr, *tauq = nullptr;
+  double *Tq = nullptr, *Ry = nullptr, *Uy = nullptr, *Vy = nullptr, *sy = nullptr, *S1 = nullptr, *S2 = nullptr;
 };
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
 
-size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& ar, RWs& w) {
+size_t layout(int64_t m, int64_t n, int64_t b, int64_t p, bool bf16, int gemm_mode, Arena& ar, RWs& w) {
   const int64_t mx = std::max(m, n);
+  const int64_t kb = b + p;  // sample width (b for randUTV_basic)
   w.hdr = reinterpret_cast<WsHeader*>(ar.take<char>(kHeaderBytes));
-  w.G = ar.take<double>(m * b);
-  w.Y = ar.take<double>(n * b);
-  w.Z = ar.take<double>(m * b);
+  w.G = ar.take<double>(m * kb);
+  w.Y = ar.take<double>(n * kb);
+  w.Z = ar.take<double>(m * kb);
   w.Yv = ar.take<double>(n * b);
   w.Yu = ar.take<double>(m * b);
   w.Xa = ar.take<double>(mx * b);
@@ -70,13 +75,28 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& 
   w.sig = ar.take<double>(b);
   w.feat = ar.take<float>(16);
   w.qdev = ar.take<int>(4);
-  w.panel_bytes = panel_scratch_bytes(mx, b);
+  if (p > 0) {
+    w.Qk = ar.take<double>(m * kb);
+    w.Xk = ar.take<double>(m * b);
+    w.Wy = ar.take<double>(n * kb);
+    w.Wn = ar.take<double>(n * p);
+    w.Yq = ar.take<double>(mx * kb);
+    w.tauq = ar.take<double>(kb);
+    w.Tq = ar.take<double>(kb * kb);
+    w.Ry = ar.take<double>(kb * kb);
+    w.Uy = ar.take<double>(kb * kb);
+    w.Vy = ar.take<double>(kb * kb);
+    w.sy = ar.take<double>(kb);
+    w.S1 = ar.take<double>(kb * kb);
+    w.S2 = ar.take<double>(kb * kb);
+  }
+  w.panel_bytes = panel_scratch_bytes(mx, kb);
   w.panel = reinterpret_cast<double*>(ar.take<char>(w.panel_bytes));
   // split-K partials of the DFMA GEMMs; between them it also serves as the small SVD's scratch
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
   const int64_t c_last = std::min(b, n - (steps - 1) * b);
-  w.gemm_bytes = std::max({(size_t)16 * mx * b * sizeof(double), jacobi_scratch_bytes(std::min(b, n)),
-                           jacobi_scratch_bytes(c_last)});
+  w.gemm_bytes = std::max({(size_t)16 * mx * kb * sizeof(double), jacobi_scratch_bytes(std::min(b, n)),
+                           jacobi_scratch_bytes(c_last), p > 0 ? jacobi_scratch_bytes(std::min(kb, n)) : 0});
   w.gemm = reinterpret_cast<double*>(ar.take<char>(w.gemm_bytes));
   w.eng.scratch = w.gemm;
   w.eng.scratch_bytes = w.gemm_bytes;
@@ -84,7 +104,7 @@ size_t layout(int64_t m, int64_t n, int64_t b, bool bf16, int gemm_mode, Arena& 
   w.eng.emulate = gemm_mode != RRF_GEMM_NATIVE;
   w.eng.force = gemm_mode == RRF_GEMM_EMULATED;
   if (w.eng.emulate) {
-    w.eng.oz_bytes = ozaki_bound(m, n, b);
+    w.eng.oz_bytes = ozaki_bound(m, n, kb);
     w.eng.oz = ar.take<char>(w.eng.oz_bytes);
   }
   if (bf16) {
@@ -187,6 +207,85 @@ cudaError_t sketch_continue(int64_t r, int64_t c, int64_t b, const double* T22, 
   return e;
 }
 
+// ---- randUTV_boosted (Algorithm 2, Secs. 4.2-4.3) ----------------------------------------------------
+
+// Explicit thin Q (rows x cols, ld ldq) of the columns of X (rows x cols, ld ldx, overwritten by the panel
+// factorization), cols <= b + p: Q = [I; 0] - Yq (Tq Yq(0:cols, :)^T).
+cudaError_t thin_q(int64_t rows, int64_t cols, double* X, int64_t ldx, double* Q, int64_t ldq, const RWs& w,
+                   cudaStream_t s) {
+  cudaError_t e = panel_qr(rows, cols, X, ldx, w.tauq, w.Yq, rows, w.Tq, cols, nullptr, 0, w.panel, w.panel_bytes,
+                           w.hdr, s, &w.eng);
+  GemmDesc g1 = gd(cols, cols, cols, w.Tq, cols, 0, w.Yq, rows, 1, w.S1, cols);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g1, 1, s);
+  if (e == cudaSuccess) e = fill_identity(rows, cols, Q, ldq, s);
+  GemmDesc g2 = gd(rows, cols, cols, w.Yq, rows, 0, w.S1, cols, 0, Q, ldq, -1.0, 1.0);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g2, 1, s);
+  return e;
+}
+
+// The c x k sample of step i (k = b + pk) into w.Y.  Without recycled directions (step 1):
+// G = randn(r, k), Y = (T22^T T22)^q T22^T G.  With them (every later step, W_next in w.Wn, ld c):
+// G = randn(r, b), Y1 = (T22^T T22)^(q-1) T22^T G, X = T22 Y1, Z = orth(T22 W_next), X <- X - Z (Z^T X),
+// Q = orth(X), Y = T22^T [Q, Z]: T22^T acts last on fresh and recycled directions alike.
+cudaError_t boosted_sample(int64_t i, int64_t r, int64_t c, int64_t b, int64_t pk, bool recycle, int q,
+                           const double* T22, int64_t ldt, uint64_t seed, const RWs& w, cudaStream_t s) {
+  const int64_t k = b + pk;
+  cudaError_t e;
+  if (!recycle) {
+    e = randn_f64(r, k, w.G, r, seed, (uint32_t)i, 1u, s);
+    if (e == cudaSuccess) e = apply_t22(true, r, c, k, T22, ldt, false, w.G, w.Y, w, s);
+    if (e == cudaSuccess) e = sketch_continue(r, c, k, T22, ldt, q, false, false, nullptr, w, s);
+    return e;
+  }
+  double* Zq = w.Qk + b * r;  // orth(T22 W_next): the last pk columns of [Q, Z]
+  e = randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s);
+  if (e == cudaSuccess) e = apply_t22(true, r, c, b, T22, ldt, false, w.G, w.Y, w, s);
+  if (e == cudaSuccess) e = sketch_continue(r, c, b, T22, ldt, q - 1, false, false, nullptr, w, s);
+  if (e == cudaSuccess) e = apply_t22(false, r, c, b, T22, ldt, false, w.Y, w.Xk, w, s);
+  if (e == cudaSuccess) e = apply_t22(false, r, c, pk, T22, ldt, false, w.Wn, w.Z, w, s);
+  if (e == cudaSuccess) e = thin_q(r, pk, w.Z, r, Zq, r, w, s);
+  GemmDesc g1 = gd(pk, b, r, Zq, r, 1, w.Xk, r, 0, w.S2, pk);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g1, 1, s);
+  GemmDesc g2 = gd(r, b, pk, Zq, r, 0, w.S2, pk, 0, w.Xk, r, -1.0, 1.0);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g2, 1, s);
+  if (e == cudaSuccess) e = thin_q(r, b, w.Xk, r, w.Qk, r, w, s);
+  if (e == cudaSuccess) e = apply_t22(true, r, c, k, T22, ldt, false, w.Qk, w.Y, w, s);
+  return e;
+}
+
+// Left singular vectors W_Y (c x k) of the sample in w.Y: Householder QR Y = Q_Y [R; 0], Jacobi SVD
+// R = U_R D V_R^T, W_Y = Q_Y [U_R; 0] = [U_R; 0] - Yq (Tq (Yq(0:k, :)^T U_R)).  Leaves W_Y(:, 0:b) in w.Y,
+// the panel that HQR_full factors into V_i.
+cudaError_t boosted_svd(int64_t c, int64_t b, int64_t k, const RWs& w, cudaStream_t s) {
+  cudaError_t e = panel_qr(c, k, w.Y, c, w.tauq, w.Yq, c, w.Tq, k, w.Ry, k, w.panel, w.panel_bytes, w.hdr, s,
+                           &w.eng);
+  if (e == cudaSuccess) e = jacobi_svd(k, w.Ry, k, w.Uy, k, w.sy, w.Vy, k, w.hdr, s, w.gemm, w.gemm_bytes);
+  if (e == cudaSuccess) e = zero_matrix(c, k, w.Wy, c, s);
+  if (e == cudaSuccess) e = copy_matrix(k, k, w.Uy, k, w.Wy, c, s);
+  GemmDesc g1 = gd(k, k, k, w.Yq, c, 1, w.Uy, k, 0, w.S1, k);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g1, 1, s);
+  GemmDesc g2 = gd(k, k, k, w.Tq, k, 0, w.S1, k, 0, w.S2, k);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g2, 1, s);
+  GemmDesc g3 = gd(c, k, k, w.Yq, c, 0, w.S2, k, 0, w.Wy, c, -1.0, 1.0);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g3, 1, s);
+  if (e == cudaSuccess) e = copy_matrix(c, b, w.Wy, c, w.Y, c, s);
+  return e;
+}
+
+// W_next = rows b.. of V_i^T W_Y(:, b:k), V_i^T = I - Yv Tv^T Yv^T: the recycled directions, expressed in
+// the columns of the next trailing block (c - b rows, ld c - b, in w.Wn).
+cudaError_t boosted_next(int64_t c, int64_t b, int64_t pk, const RWs& w, cudaStream_t s) {
+  double* Wr = w.Wy + b * c;
+  GemmDesc g1 = gd(b, pk, c, w.Yv, c, 1, Wr, c, 0, w.S1, b);
+  cudaError_t e = gemm_run(w.eng, &g1, 1, s);
+  GemmDesc g2 = gd(b, pk, b, w.Tv, b, 1, w.S1, b, 0, w.S2, b);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g2, 1, s);
+  GemmDesc g3 = gd(c, pk, b, w.Yv, c, 0, w.S2, b, 0, Wr, c, -1.0, 1.0);
+  if (e == cudaSuccess) e = gemm_run(w.eng, &g3, 1, s);
+  if (e == cudaSuccess) e = copy_matrix(c - b, pk, Wr + b, c, w.Wn, c - b, s);
+  return e;
+}
+
 rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, double* U,
                       int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, const rrf_opts* opts) {
   clear_arg_error();
@@ -209,8 +308,14 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
     }
     if (opts->q_policy != RRF_Q_FIXED && opts->q_policy != RRF_Q_LEARNED) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->q_policy == RRF_Q_LEARNED && opts->q_per_block != nullptr) { set_arg_error(16); return RRF_INVALID_ARG; }
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
       if (opts->reserved[i] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->oversample < 0 || b + opts->oversample > 256) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->oversample > 0 && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->reorth != 0 ||
+                                 opts->q_policy != RRF_Q_FIXED)) {
+      set_arg_error(16);
+      return RRF_INVALID_ARG;
+    }
     if (opts->gemm_mode < RRF_GEMM_AUTO || opts->gemm_mode > RRF_GEMM_EMULATED) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->q_per_block != nullptr) {
       const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
@@ -231,7 +336,8 @@ extern "C" size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const r
   Arena ar;
   RWs w;
   const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;
-  return layout(m, n, b, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
+  const int64_t p = opts != nullptr ? std::max(opts->oversample, 0) : 0;
+  return layout(m, n, b, p, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
 }
 
 extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
@@ -256,7 +362,8 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   ar.base = reinterpret_cast<char*>(workspace);
   ar.cap = ws_bytes;
   RWs w;
-  layout(m, n, b, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
+  const int64_t p = opts != nullptr ? opts->oversample : 0;
+  layout(m, n, b, p, bf16, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
   if (ar.overflow) return RRF_WORKSPACE_TOO_SMALL;
 
   RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
@@ -268,42 +375,53 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
 
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
   const bool learned = opts != nullptr && opts->q_policy == RRF_Q_LEARNED;
+  bool have_next = false;  // randUTV_boosted: W_next of the previous step is in w.Wn
   for (int64_t i = 1; i <= steps; ++i) {
     const int64_t o = b * (i - 1);
     const int64_t r = m - o, c = n - o;
     double* T22 = T + o + o * ldt;
     if (b * i < m && b * i < n) {
       int qi = (opts != nullptr && opts->q_per_block != nullptr) ? opts->q_per_block[i - 1] : q;
-      // Sketch.
-      RRF_CUDA_TRY(randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s));
-      RRF_CUDA_TRY(sketch_begin(r, c, b, T22, ldt, bf16, w, s));
-      const double* start = nullptr;
-      if (learned) {
-        // Features from the q = 0 sketch (the R of its Householder QR), MLP -> q for this step.
-        RRF_CUDA_TRY(copy_matrix(c, b, w.Y, c, w.Qt, c, s));
-        RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s, &w.eng));
-        RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, i > 1 ? w.sig : nullptr, (int)i, (int)steps, n, c, w.feat, s));
-        if (opts->mlp_params != nullptr) {
-          RRF_CUDA_TRY(policy_decide(opts->mlp_params, w.feat, w.qdev, s));
-          int qh = q;
-          RRF_CUDA_TRY(cudaMemcpyAsync(&qh, w.qdev, sizeof(int), cudaMemcpyDeviceToHost, s));
-          if (opts->features_out != nullptr)
+      const int64_t pk = std::min(p, c - b);  // oversampling of this step (fewer columns near the end)
+      if (p > 0) {
+        // randUTV_boosted: sample of b + pk columns; V_i from its leading b left singular vectors.
+        if (opts->q_used_out != nullptr) opts->q_used_out[i - 1] = qi;
+        RRF_CUDA_TRY(boosted_sample(i, r, c, b, pk, i > 1 && have_next, qi, T22, ldt, seed, w, s));
+        RRF_CUDA_TRY(boosted_svd(c, b, b + pk, w, s));
+      } else {
+        // randUTV_basic sketch.
+        RRF_CUDA_TRY(randn_f64(r, b, w.G, r, seed, (uint32_t)i, 1u, s));
+        RRF_CUDA_TRY(sketch_begin(r, c, b, T22, ldt, bf16, w, s));
+        const double* start = nullptr;
+        if (learned) {
+          // Features from the q = 0 sketch (the R of its Householder QR), MLP -> q for this step.
+          RRF_CUDA_TRY(copy_matrix(c, b, w.Y, c, w.Qt, c, s));
+          RRF_CUDA_TRY(panel_qr(c, b, w.Qt, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr,
+                                s, &w.eng));
+          RRF_CUDA_TRY(policy_features(w.Qt, c, (int)b, i > 1 ? w.sig : nullptr, (int)i, (int)steps, n, c, w.feat,
+                                       s));
+          if (opts->mlp_params != nullptr) {
+            RRF_CUDA_TRY(policy_decide(opts->mlp_params, w.feat, w.qdev, s));
+            int qh = q;
+            RRF_CUDA_TRY(cudaMemcpyAsync(&qh, w.qdev, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (opts->features_out != nullptr)
+              RRF_CUDA_TRY(cudaMemcpyAsync(opts->features_out + 16 * (i - 1), w.feat, 16 * sizeof(float),
+                                           cudaMemcpyDeviceToHost, s));
+            RRF_CUDA_TRY(cudaStreamSynchronize(s));
+            qi = qh;
+          } else if (opts->features_out != nullptr) {
             RRF_CUDA_TRY(cudaMemcpyAsync(opts->features_out + 16 * (i - 1), w.feat, 16 * sizeof(float),
                                          cudaMemcpyDeviceToHost, s));
-          RRF_CUDA_TRY(cudaStreamSynchronize(s));
-          qi = qh;
-        } else if (opts->features_out != nullptr) {
-          RRF_CUDA_TRY(cudaMemcpyAsync(opts->features_out + 16 * (i - 1), w.feat, 16 * sizeof(float),
-                                       cudaMemcpyDeviceToHost, s));
-          RRF_CUDA_TRY(cudaStreamSynchronize(s));
+            RRF_CUDA_TRY(cudaStreamSynchronize(s));
+          }
+          if (reorth && qi > 0) {  // the QR just computed gives the orthonormal start for free
+            RRF_CUDA_TRY(explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s));
+            start = w.Qt;
+          }
         }
-        if (reorth && qi > 0) {  // the QR just computed gives the orthonormal start for free
-          RRF_CUDA_TRY(explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s));
-          start = w.Qt;
-        }
+        if (opts != nullptr && opts->q_used_out != nullptr) opts->q_used_out[i - 1] = qi;
+        RRF_CUDA_TRY(sketch_continue(r, c, b, T22, ldt, qi, bf16, reorth, start, w, s));
       }
-      if (opts != nullptr && opts->q_used_out != nullptr) opts->q_used_out[i - 1] = qi;
-      RRF_CUDA_TRY(sketch_continue(r, c, b, T22, ldt, qi, bf16, reorth, start, w, s));
       // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
       RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,
                             w.hdr, s, &w.eng));
@@ -319,6 +437,10 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         GemmDesc g3[2] = {gd(m, c, b, w.Xc, m, 0, w.Yv, c, 1, CT, ldt, -1.0, 1.0),
                           gd(n, c, b, w.Xd, n, 0, w.Yv, c, 1, CV, ldv, -1.0, 1.0)};
         RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
+      }
+      if (p > 0) {
+        RRF_CUDA_TRY(boosted_next(c, b, pk, w, s));
+        have_next = pk > 0;
       }
       // [U_i, R] = HQR_full(T(o:, o:o+b)).
       RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, w.Rs, b, w.panel, w.panel_bytes,

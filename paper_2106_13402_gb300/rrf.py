@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("q_per_block", ctypes.POINTER(ctypes.c_int)), ("q_policy", ctypes.c_int),
                 ("mlp_params", ctypes.c_void_p), ("q_used_out", ctypes.POINTER(ctypes.c_int)),
                 ("features_out", ctypes.POINTER(ctypes.c_float)), ("gemm_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("oversample", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 Q_FIXED, Q_LEARNED = 0, 1
@@ -190,15 +190,16 @@ def _check(st: int, what: str):
 
 
 def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None, q_policy: int = Q_FIXED,
-              mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO):
+              mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO, oversample: int = 0):
     """rrf_opts.  With q_policy=Q_LEARNED, pass `steps` (= ceil(n/b)) to receive per-step q and features in
     opts.q_used / opts.features after the call; mlp_params is a CUDA float16 tensor of rrf_mlp_param_count
-    values (None: features only, q stays fixed)."""
+    values (None: features only, q stays fixed).  oversample = p > 0 selects randUTV_boosted (Algorithm 2)."""
     o = Opts()
     o.sketch_prec = int(sketch_prec)
     o.reorth = 1 if reorth else 0
     o.q_policy = int(q_policy)
     o.gemm_mode = int(gemm_mode)
+    o.oversample = int(oversample)
     keep = []
     if q_per_block is not None:
         qa = (ctypes.c_int * len(q_per_block))(*[int(v) for v in q_per_block])

@@ -73,6 +73,32 @@ def test_argument_validation_is_host_side(L, name):
     assert L.rrf_last_arg_error() == 12
 
 
+def test_oversample_option_validation(L):
+    """randUTV_boosted (Algorithm 2) is selected by opts.oversample = p > 0: 1 <= b + p <= 256, FP64 sketch,
+    no re-orthonormalization, fixed q; powerURV has no oversampling."""
+    fake = ctypes.c_void_p(0x10000)
+
+    def call(name, b, **kw):
+        o = rrf.make_opts(**kw)
+        return getattr(L, name)(40, 30, fake, 40, b, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000),
+                                1 << 20, ctypes.byref(o), None)
+
+    for kw in (dict(oversample=-1), dict(oversample=129), dict(oversample=8, sketch_prec=rrf.SKETCH_BF16),
+               dict(oversample=8, reorth=True), dict(oversample=8, q_policy=rrf.Q_LEARNED)):
+        assert call("rrf_randutv", 128, **kw) == rrf.RRF_INVALID_ARG, kw
+        assert L.rrf_last_arg_error() == 16
+    assert call("rrf_powerurv", 16, oversample=8) == rrf.RRF_UNSUPPORTED
+    o = rrf.make_opts(oversample=64)
+    o.reserved[1] = 1
+    assert L.rrf_randutv(40, 30, fake, 40, 16, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000), 1 << 20,
+                         ctypes.byref(o), None) == rrf.RRF_INVALID_ARG
+    # the boosted workspace holds the b + p column sample and its SVD
+    assert rrf.randutv_workspace_bytes(1024, 1024, 64, rrf.make_opts(oversample=64)) > \
+        rrf.randutv_workspace_bytes(1024, 1024, 64)
+    assert rrf.randutv_workspace_bytes(1024, 1024, 64, rrf.make_opts(oversample=0)) == \
+        rrf.randutv_workspace_bytes(1024, 1024, 64)
+
+
 def test_small_entry_point_validation(L):
     fake = ctypes.c_void_p(0x10000)
     assert L.rrf_gemm(b"X", b"N", 2, 2, 2, 1.0, fake, 2, fake, 2, 0.0, fake, 2, None, 0, None) == rrf.RRF_INVALID_ARG
