@@ -90,6 +90,9 @@ typedef struct rrf_opts {
                         of the sample, and the other p carried into the next step (see rrf_randutv).
                         1 <= b + p <= 256; p > 0 requires the FP64 sketch, reorth = 0 and fixed q
                         (q_per_block allowed).  0 (default) is randUTV_basic.                       */
+  double frob_tol;   /* > 0: early termination by the Frobenius recurrence of Sec. 4.1 (see rrf_randutv); 0 off */
+  double* frob_out;  /* optional HOST array [ceil(n/b) + 1]: e_0 = ||A||_F, e_1, ..., e_steps (recurrence)   */
+  int* steps_out;    /* optional HOST int: the number of steps performed                                 */
   int reserved[2];   /* must be zero */
 } rrf_opts;
 
@@ -117,6 +120,16 @@ typedef struct rrf_opts {
  * Y = T22^T [Q, Z].  Then W_Y = the left singular vectors of Y (Householder QR of Y, Jacobi SVD of its
  * k x k R, both FP64), V_i = HQR_full(W_Y(:, 1:b)) and W_next = rows b.. of V_i^T W_Y(:, b+1:k).  The
  * rest of the step (and the last step) is that of randUTV_basic.
+ *
+ * Early termination (Sec. 4.1; any sampling option).  With opts->frob_tol > 0 or opts->frob_out set, the
+ * library evaluates e_0 = ||A||_F and, after each step i, e_i^2 = max(e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2, 0)
+ * on the device (e_i = ||T(ib:, ib:)||_F up to rounding of order eps ||A||_F^2 / e_i; the last step gives
+ * e = 0).  With frob_tol > 0 the call stops after the first step i >= 0 with e_i <= frob_tol (absolute):
+ * A = U T V^T still holds with U, V orthogonal, T's first ib columns are upper trapezoidal with diagonal
+ * b x b blocks and T(ib:, ib:) is the unreduced trailing block (i = 0: T = A, U = I, V = I).  Checking the
+ * tolerance synchronizes the stream once per step, so such a call cannot be captured in a CUDA graph.
+ * frob_out receives e_0 .. e_done (written before return: with frob_tol = 0 the call synchronizes once
+ * at the end to fill it); steps_out (any mode) receives the number of steps done.
  * ---------------------------------------------------------------------------------------------- */
 RRF_API size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
 RRF_API rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,

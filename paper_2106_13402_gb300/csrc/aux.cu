@@ -1,5 +1,6 @@
 // aux.cu -- small memory-bound kernels of the drivers (initialisation of U = I, V = I, T = A; block
-// copies for the in-place small products; writing D_small and the zero blocks of Algorithm 3).
+// copies for the in-place small products; writing D_small and the zero blocks of Algorithm 3; the
+// Frobenius norms of the early-termination rule).
 #include <algorithm>
 
 #include "rrf_internal.cuh"
@@ -48,7 +49,61 @@ __global__ void finite_kernel(int64_t rows, int64_t cols, const double* __restri
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, RRF_NUMERICAL);
 }
 
+// Frobenius norms of the early-termination rule (Sec. 4.1): per-block partial sums of squares in a fixed
+// grid-stride order, then one block sums the partials in a fixed tree, so the result is repeatable.
+constexpr int kSumsqThreads = 256;
+constexpr int kSumsqMaxBlocks = 1024;
+
+__global__ void sumsq_kernel(int64_t rows, int64_t cols, const double* __restrict__ X, int64_t ld,
+                             double* __restrict__ part) {
+  __shared__ double sh[kSumsqThreads];
+  const int64_t total = rows * cols;
+  double acc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double v = X[(idx % rows) + (idx / rows) * ld];
+    acc = fma(v, v, acc);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kSumsqThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// e2[idx] = the sum of the nblk partials (first), else max(e2[idx - 1] - that sum, 0).
+__global__ void frob_update_kernel(const double* __restrict__ part, int nblk, double* e2, int64_t idx, int first) {
+  __shared__ double sh[kSumsqMaxBlocks];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < nblk; t += blockDim.x) acc += part[t];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kSumsqMaxBlocks / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) e2[idx] = first ? sh[0] : fmax(e2[idx - 1] - sh[0], 0.0);
+}
+
 }  // namespace
+
+size_t frob_scratch_bytes() { return kSumsqMaxBlocks * sizeof(double); }
+
+cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2, int64_t idx,
+                      bool first, cudaStream_t s) {
+  const int64_t total = std::max<int64_t>(rows, 0) * std::max<int64_t>(cols, 0);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 4 * kSumsqThreads - 1) / (4 * kSumsqThreads),
+                                                              kSumsqMaxBlocks));
+  sumsq_kernel<<<(unsigned)grid, kSumsqThreads, 0, s>>>(total > 0 ? rows : 1, total > 0 ? cols : 0, X, ld, part);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  frob_update_kernel<<<1, kSumsqMaxBlocks, 0, s>>>(part, (int)grid, e2, idx, first ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {
   return launch(kIdentity, rows, cols, nullptr, 0, X, ld, nullptr, s);

@@ -13,6 +13,7 @@
 // default); the BF16 sketch and the learned per-step q are options.  Everything is enqueued on the
 // caller's stream and nothing is allocated; the learned policy synchronizes once per step.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "rrf_internal.cuh"
@@ -45,6 +46,8 @@ struct RWs {
   // V_R, D), the left singular vectors W_Y, the recycled directions W_next, thin-Q scratch.
   double *Qk = nullptr, *Xk = nullptr, *Wy = nullptr, *Wn = nullptr, *Yq = nullptr, *tauq = nullptr;
   double *Tq = nullptr, *Ry = nullptr, *Uy = nullptr, *Vy = nullptr, *sy = nullptr, *S1 = nullptr, *S2 = nullptr;
+  // early termination: e_i^2 of the Frobenius recurrence (steps + 1) and the reduction's partial sums
+  double *e2 = nullptr, *fpart = nullptr;
 };
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
@@ -75,6 +78,8 @@ size_t layout(int64_t m, int64_t n, int64_t b, int64_t p, bool bf16, int gemm_mo
   w.sig = ar.take<double>(b);
   w.feat = ar.take<float>(16);
   w.qdev = ar.take<int>(4);
+  w.e2 = ar.take<double>(std::min((m + b - 1) / b, (n + b - 1) / b) + 1);
+  w.fpart = reinterpret_cast<double*>(ar.take<char>(frob_scratch_bytes()));
   if (p > 0) {
     w.Qk = ar.take<double>(m * kb);
     w.Xk = ar.take<double>(m * b);
@@ -311,6 +316,7 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
     for (int i = 0; i < 2; ++i)
       if (opts->reserved[i] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->oversample < 0 || b + opts->oversample > 256) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (!(opts->frob_tol >= 0.0) || std::isinf(opts->frob_tol)) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->oversample > 0 && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->reorth != 0 ||
                                  opts->q_policy != RRF_Q_FIXED)) {
       set_arg_error(16);
@@ -376,7 +382,23 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
   const bool learned = opts != nullptr && opts->q_policy == RRF_Q_LEARNED;
   bool have_next = false;  // randUTV_boosted: W_next of the previous step is in w.Wn
-  for (int64_t i = 1; i <= steps; ++i) {
+  // Early termination (Sec. 4.1): e_0 = ||A||_F, then the recurrence after every step.
+  const double frob_tol = opts != nullptr ? opts->frob_tol : 0.0;
+  const bool frob = opts != nullptr && (frob_tol > 0.0 || opts->frob_out != nullptr);
+  auto below_tol = [&](int64_t idx, bool* stop) -> cudaError_t {
+    double e2 = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&e2, w.e2 + idx, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *stop = e2 <= frob_tol * frob_tol;
+    return e;
+  };
+  bool stop = false;
+  int64_t done = 0;
+  if (frob) {
+    RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, s));
+    if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(0, &stop));
+  }
+  for (int64_t i = 1; i <= steps && !stop; ++i) {
     const int64_t o = b * (i - 1);
     const int64_t r = m - o, c = n - o;
     double* T22 = T + o + o * ldt;
@@ -478,6 +500,10 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         if (o > 0) RRF_CUDA_TRY(copy_matrix(o, b, w.Xc, o, TI1J2, ldt, s));
         RRF_CUDA_TRY(set_diag_block(r, b, w.sig, T22, ldt, s));
       }
+      if (frob) {  // e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2
+        RRF_CUDA_TRY(frob_step(b, c, T22, ldt, w.fpart, w.e2, i, false, s));
+        if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(i, &stop));
+      }
     } else {
       // Final block: SVD of the r x c remainder (c <= b).
       const double* M = T22;
@@ -508,7 +534,16 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       RRF_CUDA_TRY(copy_matrix(n, c, w.Xb, n, VJ, ldv, s));
       if (o > 0) RRF_CUDA_TRY(copy_matrix(o, c, w.Xc, o, TI1J, ldt, s));
       RRF_CUDA_TRY(set_diag_block(r, c, w.sig, T22, ldt, s));
+      if (frob) RRF_CUDA_TRY(cudaMemsetAsync(w.e2 + i, 0, sizeof(double), s));  // nothing left
     }
+    done = i;
+  }
+  if (opts != nullptr && opts->steps_out != nullptr) *opts->steps_out = (int)done;
+  if (opts != nullptr && opts->frob_out != nullptr) {
+    std::vector<double> e2((size_t)done + 1);
+    RRF_CUDA_TRY(cudaMemcpyAsync(e2.data(), w.e2, e2.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RRF_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t j = 0; j < e2.size(); ++j) opts->frob_out[j] = std::sqrt(e2[j]);
   }
   return RRF_OK;
 }

@@ -167,6 +167,11 @@ cudaError_t set_diag_block(int64_t rows, int64_t cols, const double* d, double* 
                            cudaStream_t s);
 // zero the strictly lower triangle of an rows x cols block
 cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
+// Frobenius recurrence (Sec. 4.1): e2[idx] = ||X||_F^2 (first) or max(e2[idx - 1] - ||X||_F^2, 0); part holds
+// frob_scratch_bytes() of partial sums.
+size_t frob_scratch_bytes();
+cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2, int64_t idx,
+                      bool first, cudaStream_t s);
 // status |= NUMERICAL if any entry of the block is not finite
 cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status,
                          cudaStream_t s);

@@ -47,7 +47,9 @@ class Opts(ctypes.Structure):
                 ("q_per_block", ctypes.POINTER(ctypes.c_int)), ("q_policy", ctypes.c_int),
                 ("mlp_params", ctypes.c_void_p), ("q_used_out", ctypes.POINTER(ctypes.c_int)),
                 ("features_out", ctypes.POINTER(ctypes.c_float)), ("gemm_mode", ctypes.c_int),
-                ("oversample", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("oversample", ctypes.c_int), ("frob_tol", ctypes.c_double),
+                ("frob_out", ctypes.POINTER(ctypes.c_double)), ("steps_out", ctypes.POINTER(ctypes.c_int)),
+                ("reserved", ctypes.c_int * 2)]
 
 
 Q_FIXED, Q_LEARNED = 0, 1
@@ -190,17 +192,33 @@ def _check(st: int, what: str):
 
 
 def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None, q_policy: int = Q_FIXED,
-              mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO, oversample: int = 0):
+              mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO, oversample: int = 0,
+              frob_tol: float = 0.0, track_frob: bool = False):
     """rrf_opts.  With q_policy=Q_LEARNED, pass `steps` (= ceil(n/b)) to receive per-step q and features in
     opts.q_used / opts.features after the call; mlp_params is a CUDA float16 tensor of rrf_mlp_param_count
-    values (None: features only, q stays fixed).  oversample = p > 0 selects randUTV_boosted (Algorithm 2)."""
+    values (None: features only, q stays fixed).  oversample = p > 0 selects randUTV_boosted (Algorithm 2).
+    frob_tol > 0 stops at the first step whose trailing Frobenius norm e_i <= frob_tol (Sec. 4.1);
+    with track_frob (needs `steps`) opts_frob(o) returns e_0 .. e_done and opts_steps_done(o) the count."""
     o = Opts()
     o.sketch_prec = int(sketch_prec)
     o.reorth = 1 if reorth else 0
     o.q_policy = int(q_policy)
     o.gemm_mode = int(gemm_mode)
     o.oversample = int(oversample)
+    o.frob_tol = float(frob_tol)
     keep = []
+    if track_frob or frob_tol > 0:
+        sd = ctypes.c_int(-1)
+        o.steps_out = ctypes.pointer(sd)
+        keep.append(sd)
+        o._steps_done = sd
+    if track_frob:
+        if steps <= 0:
+            raise ValueError("track_frob needs steps = ceil(n / b)")
+        fr = (ctypes.c_double * (steps + 1))()
+        o.frob_out = ctypes.cast(fr, ctypes.POINTER(ctypes.c_double))
+        keep.append(fr)
+        o._frob = fr
     if q_per_block is not None:
         qa = (ctypes.c_int * len(q_per_block))(*[int(v) for v in q_per_block])
         o.q_per_block = ctypes.cast(qa, ctypes.POINTER(ctypes.c_int))
@@ -217,6 +235,16 @@ def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=
         o._qu, o._fo, o._steps = qu, fo, steps
     o._keep = keep
     return o
+
+
+def opts_steps_done(o) -> int:
+    """Number of randUTV steps the last call with these options performed."""
+    return int(o._steps_done.value)
+
+
+def opts_frob(o):
+    """e_0 = ||A||_F, e_1, ..., e_done of the Frobenius recurrence (Sec. 4.1) from the last call."""
+    return [float(o._frob[j]) for j in range(opts_steps_done(o) + 1)]
 
 
 def opts_q_used(o):

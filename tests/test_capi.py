@@ -99,6 +99,36 @@ def test_oversample_option_validation(L):
         rrf.randutv_workspace_bytes(1024, 1024, 64)
 
 
+def test_opts_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of rrf_opts has the C struct's size and field offsets (compiled from include/rrf.h)."""
+    fields = [f[0] for f in rrf.Opts._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rrf.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(rrf_opts));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(rrf_opts, {f}));\n' for f in fields) + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(rrf.Opts)
+    assert out[1:] == [getattr(rrf.Opts, f).offset for f in fields]
+
+
+def test_frobenius_option_validation(L):
+    fake = ctypes.c_void_p(0x10000)
+    for tol in (-1.0, float("nan"), float("inf")):
+        o = rrf.make_opts(frob_tol=tol if tol == tol and tol > 0 else 0.0)
+        o.frob_tol = tol
+        assert L.rrf_randutv(40, 30, fake, 40, 16, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000),
+                             1 << 20, ctypes.byref(o), None) == rrf.RRF_INVALID_ARG
+        assert L.rrf_last_arg_error() == 16
+    o = rrf.make_opts(frob_tol=1e-3)
+    assert L.rrf_powerurv(40, 30, fake, 40, 16, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000),
+                          1 << 20, ctypes.byref(o), None) == rrf.RRF_UNSUPPORTED
+    with pytest.raises(ValueError):
+        rrf.make_opts(track_frob=True)
+
+
 def test_small_entry_point_validation(L):
     fake = ctypes.c_void_p(0x10000)
     assert L.rrf_gemm(b"X", b"N", 2, 2, 2, 1.0, fake, 2, fake, 2, 0.0, fake, 2, None, 0, None) == rrf.RRF_INVALID_ARG

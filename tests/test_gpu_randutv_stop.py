@@ -1,0 +1,97 @@
+"""GPU randUTV with early termination by the Frobenius recurrence (Sec. 4.1: e_0 = ||A||_F,
+e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2), through the C ABI, against the FP64 oracle.
+
+e_i is the Frobenius norm of the trailing block after step i; later steps only rotate that block, so the
+oracle's complete factorization gives every e_i as ||To(ib:, ib:)||_F.  Tolerances: the recurrence's e_i^2
+within 1e-12 ||A||_F^2 of the oracle's (its cancellation error is of order eps ||A||_F^2 per step); a
+stopped factorization keeps A = U T V^T and orthogonality to 1e-12, its first ib columns upper trapezoidal
+with diagonal b x b blocks (exact zeros), and ||T(ib:, ib:)||_F within 1e-10 relative of the oracle's e_i.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2106_13402_gb300 import rrf, testmats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    rrf.lib()
+
+
+def dev(x):
+    return rrf.as_fortran(torch.from_numpy(np.asfortranarray(x)).cuda())
+
+
+def host(x):
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+def run(A, b, q, seed, **kw):
+    n = A.shape[1]
+    o = rrf.make_opts(track_frob=True, steps=-(-n // b), **kw)
+    U, T, V = (host(x) for x in rrf.randutv(dev(A), b, q, seed=seed, opts=o))
+    return U, T, V, rrf.opts_steps_done(o), rrf.opts_frob(o)
+
+
+def oracle_e(A, b, q, seed, p=0):
+    n = A.shape[1]
+    Uo, To, Vo, st = oracle.randutv_boosted(A, b, q, p, seed) if p else oracle.randutv(A, b, q, seed)
+    assert st == 0
+    return [np.linalg.norm(To[k * b:, k * b:]) for k in range(-(-n // b) + 1)]
+
+
+CASES = [(300, 250, 32, 1, 0, "exp8"), (257, 129, 16, 2, 0, "fast"), (300, 250, 32, 1, 32, "exp8")]
+
+
+@pytest.mark.parametrize("m,n,b,q,p,prof", CASES)
+def test_frobenius_recurrence_matches_oracle(m, n, b, q, p, prof):
+    A, s = testmats.make_matrix(m, n, prof, 3, 4)
+    U, T, V, done, fr = run(A, b, q, 11, oversample=p)
+    eo = oracle_e(A, b, q, 11, p)
+    assert done == len(eo) - 1
+    assert fr[-1] == 0.0
+    nA2 = np.linalg.norm(A) ** 2
+    for k in range(len(eo)):
+        assert abs(fr[k] ** 2 - eo[k] ** 2) <= 1e-12 * nA2, (k, fr[k], eo[k])
+
+
+@pytest.mark.parametrize("m,n,b,q,p,prof", CASES)
+@pytest.mark.parametrize("kstop", [0, 1, 3])
+def test_tolerance_stops_at_first_step_below(m, n, b, q, p, prof, kstop):
+    A, s = testmats.make_matrix(m, n, prof, 3, 4)
+    eo = oracle_e(A, b, q, 11, p)
+    tol = np.sqrt(eo[kstop] * eo[kstop + 1])
+    U, T, V, done, fr = run(A, b, q, 11, oversample=p, frob_tol=tol)
+    assert done == kstop + 1
+    res = np.linalg.norm(A - U @ T @ V.T) / np.linalg.norm(A)
+    assert res <= 1e-12
+    assert np.abs(U.T @ U - np.eye(m)).max() <= 1e-12
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
+    k = done * b
+    assert np.all(np.tril(T[:, :k], -1) == 0.0)
+    for o in range(0, k, b):
+        blk = T[o:o + b, o:o + b]
+        assert np.all(blk * (1.0 - np.eye(*blk.shape)) == 0.0)
+    tail = np.linalg.norm(T[k:, k:])
+    assert abs(tail - eo[done]) <= 1e-10 * eo[done]
+    assert abs(fr[-1] ** 2 - eo[done] ** 2) <= 1e-12 * np.linalg.norm(A) ** 2
+    assert fr[-1] <= tol < fr[-2]
+
+
+def test_tolerance_above_norm_does_no_step():
+    A, s = testmats.make_matrix(100, 80, "exp8", 3, 4)
+    U, T, V, done, fr = run(A, 32, 1, 11, frob_tol=2 * np.linalg.norm(A))
+    assert done == 0
+    assert np.array_equal(T, A)
+    assert np.array_equal(U, np.eye(100)) and np.array_equal(V, np.eye(80))
+    assert abs(fr[0] - np.linalg.norm(A)) <= 1e-13 * np.linalg.norm(A)
