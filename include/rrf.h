@@ -5,6 +5,10 @@
  * V (n x n) are orthogonal and T (m x n) is upper trapezoidal, by one of the paper's two methods:
  *   rrf_randutv  -- blocked randUTV_basic (Algorithm 3; Sec. 4.1);
  *   rrf_powerurv -- powerURV (Algorithm 1; Sec. 3.2).
+ * For m < n both factor A^T instead and transpose the result (Sec. 1.3 footnote): with A^T = U' T' V'^T
+ * they return U = V' (m x m), T = T'^T (m x n, LOWER trapezoidal: zero above the diagonal; for randUTV
+ * with diagonal b x b blocks) and V = U' (n x n), so A = U T V^T still holds.  The workspace query covers
+ * A^T and T'; the status word stays at the start of the workspace.
  *
  * Common conventions (every entry point):
  *  - Matrices are column-major FP64 with an explicit leading dimension (ld >= rows).  Unless an entry
@@ -51,7 +55,7 @@ typedef enum {
   RRF_NOT_CONVERGED = 3,    /* a b x b Jacobi SVD reached its 40-sweep cap (result still written) */
   RRF_TIMEOUT = 4,          /* a bounded device-side wait (grid or cluster barrier) gave up       */
   RRF_NUMERICAL = 5,        /* non-finite value met                                              */
-  RRF_UNSUPPORTED = 6,      /* shape or option this build does not handle (e.g. m < n)           */
+  RRF_UNSUPPORTED = 6,      /* option this entry point does not handle (e.g. oversampling in powerURV) */
   RRF_WORKSPACE_TOO_SMALL = 7
 } rrf_status;
 
@@ -102,7 +106,7 @@ typedef struct rrf_opts {
  * V <- V V_i, U_i and R from HQR_full(T(I2 u I3, J2)), U <- U U_i, T(I2 u I3, J3) <- U_i^T T,
  * T(I3, J2) = 0, then the SVD of R(1:b, 1:b) makes T(I2, J2) diagonal (descending, >= 0).  The last
  * step takes the SVD of the remaining block (via HQR then SVD when it is tall, Sec. 4.2).
- *   m, n      : rows, columns; 1 <= n <= m.
+ *   m, n      : rows, columns, >= 1 (m < n: through A^T, see the top of this file).
  *   A, lda    : input (device), lda >= m.
  *   b         : block size, 1 <= b <= 256.
  *   q         : power-iteration count, 0 <= q <= 16.

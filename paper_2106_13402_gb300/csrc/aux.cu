@@ -8,7 +8,7 @@
 namespace rrf {
 namespace {
 
-enum Op { kIdentity = 0, kCopy = 1, kZero = 2, kDiag = 3, kZeroLower = 4 };
+enum Op { kIdentity = 0, kCopy = 1, kZero = 2, kDiag = 3, kZeroLower = 4, kTranspose = 5 };
 
 __global__ void block_kernel(int op, int64_t rows, int64_t cols, const double* __restrict__ S, int64_t lds,
                              double* __restrict__ D, int64_t ldd, const double* __restrict__ d) {
@@ -23,6 +23,7 @@ __global__ void block_kernel(int op, int64_t rows, int64_t cols, const double* _
       case kZero: *dst = 0.0; break;
       case kDiag: *dst = (i == j) ? d[i] : 0.0; break;
       case kZeroLower: if (i > j) *dst = 0.0; break;
+      case kTranspose: D[j + i * ldd] = S[i + j * lds]; break;  // D is cols x rows
     }
   }
 }
@@ -117,6 +118,10 @@ cudaError_t zero_matrix(int64_t rows, int64_t cols, double* X, int64_t ld, cudaS
 }
 cudaError_t set_diag_block(int64_t rows, int64_t cols, const double* d, double* X, int64_t ld, cudaStream_t s) {
   return launch(kDiag, rows, cols, nullptr, 0, X, ld, d, s);
+}
+cudaError_t transpose_matrix(int64_t rows, int64_t cols, const double* S, int64_t lds, double* D, int64_t ldd,
+                             cudaStream_t s) {
+  return launch(kTranspose, rows, cols, S, lds, D, ldd, nullptr, s);
 }
 cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {
   return launch(kZeroLower, rows, cols, nullptr, 0, X, ld, nullptr, s);

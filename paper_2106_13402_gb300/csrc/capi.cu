@@ -202,19 +202,60 @@ extern "C" rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, do
   return RRF_OK;
 }
 
+// ---- m < n: factor A^T and transpose the result (Sec. 1.3 footnote) ---------------------------------------
+namespace rrf {
+
+size_t wide_workspace(WsFn wsfn, int64_t m, int64_t n, int64_t b, const rrf_opts* opts) {
+  const size_t inner = wsfn(n, m, b, opts);
+  if (inner == 0) return 0;
+  return align_up(inner, 256) + 2 * align_up(sizeof(double) * (size_t)m * (size_t)n, 256);
+}
+
+rrf_status factor_wide(WsFn wsfn, RunFn run, int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                       double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, uint64_t seed,
+                       void* workspace, size_t ws_bytes, const rrf_opts* opts, void* stream_) {
+  clear_arg_error();
+  if (A == nullptr) { set_arg_error(3); return RRF_INVALID_ARG; }
+  if (lda < m) { set_arg_error(4); return RRF_INVALID_ARG; }
+  if (b < 1 || b > 256) { set_arg_error(5); return RRF_INVALID_ARG; }
+  if (U == nullptr) { set_arg_error(7); return RRF_INVALID_ARG; }
+  if (ldu < m) { set_arg_error(8); return RRF_INVALID_ARG; }
+  if (T == nullptr) { set_arg_error(9); return RRF_INVALID_ARG; }
+  if (ldt < m) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (V == nullptr) { set_arg_error(11); return RRF_INVALID_ARG; }
+  if (ldv < n) { set_arg_error(12); return RRF_INVALID_ARG; }
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
+    set_arg_error(14);
+    return RRF_INVALID_ARG;
+  }
+  // The tall call checks q and the options; with no workspace it stops before enqueuing anything.
+  const rrf_status v = run(n, m, A, n, b, q, V, ldv, T, n, U, ldu, seed, workspace, 0, opts, stream_);
+  if (v != RRF_WORKSPACE_TOO_SMALL && v != RRF_OK) return v;
+  clear_arg_error();
+  const size_t inner = wsfn(n, m, b, opts);
+  if (ws_bytes < wide_workspace(wsfn, m, n, b, opts)) { set_arg_error(15); return RRF_WORKSPACE_TOO_SMALL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  double* At = reinterpret_cast<double*>(reinterpret_cast<char*>(workspace) + align_up(inner, 256));
+  double* Tt = reinterpret_cast<double*>(reinterpret_cast<char*>(At) +
+                                         align_up(sizeof(double) * (size_t)m * (size_t)n, 256));
+  RRF_CUDA_TRY(transpose_matrix(m, n, A, lda, At, n, s));
+  // A^T (n x m, tall) = U' T' V'^T: U' (n x n) lands in V, V' (m x m) in U.
+  const rrf_status r = run(n, m, At, n, b, q, V, ldv, Tt, n, U, ldu, seed, workspace, inner, opts, stream_);
+  if (r != RRF_OK) return r;
+  RRF_CUDA_TRY(transpose_matrix(n, m, Tt, n, T, ldt, s));
+  return RRF_OK;
+}
+
+}  // namespace rrf
+
 // ---- host-buffer forms -----------------------------------------------------------------------------
 namespace {
-
-typedef size_t (*WsFn)(int64_t, int64_t, int64_t, const rrf_opts*);
-typedef rrf_status (*RunFn)(int64_t, int64_t, const double*, int64_t, int64_t, int, double*, int64_t, double*,
-                            int64_t, double*, int64_t, uint64_t, void*, size_t, const rrf_opts*, void*);
 
 rrf_status run_host(WsFn wsfn, RunFn run, int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
                     double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, uint64_t seed,
                     const rrf_opts* opts, void* stream_) {
   clear_arg_error();
   if (m < 1 || n < 1) { set_arg_error(m < 1 ? 1 : 2); return RRF_INVALID_ARG; }
-  if (m < n) { set_arg_error(1); return RRF_UNSUPPORTED; }
   if (A == nullptr || lda < m) { set_arg_error(A == nullptr ? 3 : 4); return RRF_INVALID_ARG; }
   if (U == nullptr || ldu < m) { set_arg_error(U == nullptr ? 7 : 8); return RRF_INVALID_ARG; }
   if (T == nullptr || ldt < m) { set_arg_error(T == nullptr ? 9 : 10); return RRF_INVALID_ARG; }

@@ -118,6 +118,7 @@ using namespace rrf;
 
 extern "C" size_t rrf_powerurv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts) {
   if (m < 1 || n < 1 || b < 1) return 0;
+  if (m < n) return wide_workspace(rrf_powerurv_workspace, m, n, b, opts);
   Arena ar;
   PWs w;
   return layout(m, n, b, opts ? opts->gemm_mode : RRF_GEMM_AUTO, ar, w);
@@ -130,7 +131,9 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   clear_arg_error();
   if (m < 1) { set_arg_error(1); return RRF_INVALID_ARG; }
   if (n < 1) { set_arg_error(2); return RRF_INVALID_ARG; }
-  if (m < n) { set_arg_error(1); return RRF_UNSUPPORTED; }
+  if (m < n)  // wide: factor A^T and transpose the result
+    return factor_wide(rrf_powerurv_workspace, rrf_powerurv, m, n, A, lda, b, q, U, ldu, T, ldt, V, ldv, seed,
+                       workspace, ws_bytes, opts, stream_);
   if (A == nullptr) { set_arg_error(3); return RRF_INVALID_ARG; }
   if (lda < m) { set_arg_error(4); return RRF_INVALID_ARG; }
   if (b < 1 || b > 256) { set_arg_error(5); return RRF_INVALID_ARG; }

@@ -296,7 +296,6 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
   clear_arg_error();
   if (m < 1) { set_arg_error(1); return RRF_INVALID_ARG; }
   if (n < 1) { set_arg_error(2); return RRF_INVALID_ARG; }
-  if (m < n) { set_arg_error(1); return RRF_UNSUPPORTED; }
   if (A == nullptr) { set_arg_error(3); return RRF_INVALID_ARG; }
   if (lda < m) { set_arg_error(4); return RRF_INVALID_ARG; }
   if (b < 1 || b > 256) { set_arg_error(5); return RRF_INVALID_ARG; }
@@ -339,6 +338,7 @@ using namespace rrf;
 
 extern "C" size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts) {
   if (m < 1 || n < 1 || b < 1) return 0;
+  if (m < n) return wide_workspace(rrf_randutv_workspace, m, n, b, opts);
   Arena ar;
   RWs w;
   const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;
@@ -350,6 +350,9 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
                                   double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
                                   uint64_t seed, void* workspace, size_t ws_bytes, const rrf_opts* opts,
                                   void* stream_) {
+  if (m >= 1 && n > m)  // wide: factor A^T and transpose the result
+    return factor_wide(rrf_randutv_workspace, rrf_randutv, m, n, A, lda, b, q, U, ldu, T, ldt, V, ldv, seed,
+                       workspace, ws_bytes, opts, stream_);
   rrf_status st = check_args(m, n, A, lda, b, q, U, ldu, T, ldt, V, ldv, opts);
   if (st != RRF_OK) return st;
   const bool bf16 = opts != nullptr && opts->sketch_prec == RRF_SKETCH_BF16;

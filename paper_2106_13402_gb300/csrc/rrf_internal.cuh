@@ -165,6 +165,9 @@ cudaError_t zero_matrix(int64_t rows, int64_t cols, double* X, int64_t ld, cudaS
 // X(0:rows, 0:cols) = [diag(d); 0] (d has min(rows, cols) entries)
 cudaError_t set_diag_block(int64_t rows, int64_t cols, const double* d, double* X, int64_t ld,
                            cudaStream_t s);
+// D (cols x rows, ldd) = S^T (S rows x cols, lds)
+cudaError_t transpose_matrix(int64_t rows, int64_t cols, const double* S, int64_t lds, double* D, int64_t ldd,
+                             cudaStream_t s);
 // zero the strictly lower triangle of an rows x cols block
 cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
 // Frobenius recurrence (Sec. 4.1): e2[idx] = ||X||_F^2 (first) or max(e2[idx - 1] - ||X||_F^2, 0); part holds
@@ -175,6 +178,18 @@ cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, d
 // status |= NUMERICAL if any entry of the block is not finite
 cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status,
                          cudaStream_t s);
+
+// ---- m < n through the transpose (capi.cu) ------------------------------------------------------------
+typedef size_t (*WsFn)(int64_t, int64_t, int64_t, const rrf_opts*);
+typedef rrf_status (*RunFn)(int64_t, int64_t, const double*, int64_t, int64_t, int, double*, int64_t, double*,
+                            int64_t, double*, int64_t, uint64_t, void*, size_t, const rrf_opts*, void*);
+// Workspace of a wide (m < n) call: the tall call's workspace first (its status word stays at the start),
+// then A^T (n x m) and the tall call's T (n x m).
+size_t wide_workspace(WsFn wsfn, int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
+// A (m x n, m < n) = U T V^T from the tall factorization A^T = U' T' V'^T: U = V', T = T'^T, V = U'.
+rrf_status factor_wide(WsFn wsfn, RunFn run, int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,
+                       double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, uint64_t seed,
+                       void* workspace, size_t ws_bytes, const rrf_opts* opts, void* stream);
 
 }  // namespace rrf
 

@@ -52,9 +52,19 @@ def _call(L, name, m, n, lda, b, q, ldu, ldt, ldv, ws=1 << 20, nullA=False):
 
 @pytest.mark.parametrize("name", ["rrf_randutv", "rrf_powerurv"])
 def test_argument_validation_is_host_side(L, name):
-    # m < n: unsupported (factor A^T instead, Sec. 4 footnote)
-    assert _call(L, name, 10, 20, 10, 4, 1, 10, 10, 20) == rrf.RRF_UNSUPPORTED
-    assert L.rrf_last_arg_error() == 1
+    # m < n goes through A^T (Sec. 1.3 footnote); its arguments keep their own meaning
+    assert _call(L, name, 10, 20, 9, 4, 1, 10, 10, 20) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 4
+    assert _call(L, name, 10, 20, 10, 4, 1, 9, 10, 20) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 8
+    assert _call(L, name, 10, 20, 10, 4, 1, 10, 10, 19) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 12
+    assert _call(L, name, 10, 20, 10, 4, -1, 10, 10, 20) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 6
+    assert _call(L, name, 10, 20, 10, 300, 1, 10, 10, 20) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 5
+    assert _call(L, name, 10, 20, 10, 4, 1, 10, 10, 20, ws=64) == rrf.RRF_WORKSPACE_TOO_SMALL
+    assert L.rrf_last_arg_error() == 15
     assert _call(L, name, 0, 0, 1, 4, 1, 1, 1, 1) == rrf.RRF_INVALID_ARG
     assert _call(L, name, 20, 10, 20, 4, 1, 20, 20, 10, nullA=True) == rrf.RRF_INVALID_ARG
     assert L.rrf_last_arg_error() == 3
