@@ -53,10 +53,12 @@ def parse():
                    help="FP64 products: library default, DFMA only, or emulated on the BF16 tensor cores")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 (DFMA) comparison run")
     p.add_argument("--no-per-method", action="store_true", help="skip the per-method timing runs (profiling)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "gemm"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "gemm", "boosted"],
                    help="c2: FP64 randUTV + powerURV 8192^2 (default); c3: BF16-sketch randUTV 16384^2, b=256, q=2; "
                         "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128; "
-                        "gemm: the dominant kernel alone (FP64 GEMM 4096^3 emulated on the tensor cores)")
+                        "gemm: the dominant kernel alone (FP64 GEMM 4096^3 emulated on the tensor cores); "
+                        "boosted: randUTV_boosted 8192^2, b=128, q=2, p=--oversample")
+    p.add_argument("--oversample", type=int, default=128, help="p of the boosted workload")
     return p.parse_args()
 
 
@@ -554,6 +556,76 @@ def run_c3_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_boosted(args):
+    """randUTV_boosted (Algorithm 2) on the 8192^2 spectrum: 8192^2, b = 128, q = 2, p = --oversample (default
+    b), the paper's remedy for e_k above 1.1 sigma_{k+1} at block boundaries.  Timed against randUTV_basic with
+    the same q and routing and against the plain FP64 method (DFMA products) of the same boosted algorithm;
+    e_k / sigma_{k+1} at every block boundary for each."""
+    torch, dev = _setup_single_gpu(args)
+    from paper_2106_13402_gb300 import rrf, testmats
+    n, b, q, p = 8192, 128, 2, args.oversample
+    A, s = testmats.make_matrix(n, n, "c2", 11, 12, device=str(dev))
+    fast = rrf.make_opts(oversample=p)
+    basic = rrf.make_opts()
+    plain = rrf.make_opts(oversample=p, gemm_mode=rrf.GEMM_NATIVE)
+    out = (rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev))
+    ks = list(range(b, n, b))
+    ws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, fast), dev)
+    for _ in range(args.warmup):
+        rrf.randutv(A, b, q, 17, opts=fast, ws=ws, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = rrf.launch_count()
+    rrf.gemm_profile_begin(200000)
+    ms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=fast, ws=ws, out=out, check_status=False), args.steps)
+    rrf.gemm_profile_end()
+    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    launches = rrf.launch_count() - l0
+    clocks = sampler.stop()
+    st = rrf.lib().rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None))
+    U, T, V = out
+    res = float(torch.linalg.norm(A - U @ T @ V.t()) / torch.linalg.norm(A))
+    r_fast = _boundary_ratios(torch, T, s, b, ks)
+    del ws
+    # randUTV_basic, same q and routing
+    bws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, basic), dev)
+    rrf.randutv(A, b, q, 17, opts=basic, ws=bws, out=out)
+    bms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=basic, ws=bws, out=out, check_status=False), args.steps)
+    r_basic = _boundary_ratios(torch, out[1], s, b, ks)
+    del bws
+    # the plain FP64 method: the same boosted algorithm with DFMA products, one timed run
+    pws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, plain), dev)
+    rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out)
+    pms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=plain, ws=pws, out=out, check_status=False), 1)
+    r_plain = _boundary_ratios(torch, out[1], s, b, ks)
+    del pws
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["bf16_tflops_sustained"])
+    ach = emu_tflops / (emu_ms / 1e3) / 1e12 if emu_ms > 0 else 0.0
+    on_target = lambda r: sum(1 for v in r.values() if v <= 1.1)
+    line = {
+        "metric": f"factorizations/s (randUTV_boosted, 8192^2, b=128, q=2, p={p}) vs plain FP64",
+        "value": round(1e3 / ms, 5), "unit": "factorizations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "randUTV_boosted 8192x8192 A = Q1 diag(s) Q2^T (s_j = 10^(-8j/n), j < n/2, then "
+                               "1e-4)", "m": n, "n": n, "b": b, "q": q, "p": p, "l2": "inputs larger than L2"},
+        "plain_fp64": {"ms": round(pms, 1), "value": round(1e3 / pms, 5), "speedup": round(pms / ms, 3),
+                       "max_ratio": max(r_plain.values()), "on_target": on_target(r_plain)},
+        "basic_same_q": {"ms": round(bms, 1), "max_ratio": max(r_basic.values()), "on_target": on_target(r_basic)},
+        "max_ratio": max(r_fast.values()), "on_target": on_target(r_fast), "boundaries": len(ks),
+        "e_k_over_sigma_k+1": r_fast,
+        "residual": res, "device_status": int(st), "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_src} bf16_tflops_sustained",
+                     "share_of_step": round(emu_ms / (ms * args.steps), 4), "launches": int(emu_launches)},
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_c4(args):
     """512 FP32 powerURV factorizations (q = 1) of uneven shape, m ~ U[256, 2048], n ~ U[128, m], mixed decays,
     in one CUDA graph of persistent batched kernels with autotuned tiles."""
@@ -665,6 +737,8 @@ def main():
         run_c4(args)
     elif args.workload == "gemm":
         run_gemm(args)
+    elif args.workload == "boosted":
+        run_boosted(args)
     else:
         run_ours(args)
 
