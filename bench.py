@@ -332,11 +332,11 @@ def run_ours(args):
         orth_u = float((U.t() @ U - eye).abs().max())
         orth_v = float((V.t() @ V - eye).abs().max())
         lower_zero = bool((torch.tril(T, -1) == 0).all())
-        ratios = {}
-        for k in (b, 16 * b, n // 2, n - 2 * b):
-            ratios[str(k)] = round(power_norm(torch, T[k:, k:]) / float(s[k]), 5)
+        ratios = _boundary_ratios(torch, T, s, b, list(range(b, n, b)))   # every block boundary
         accuracy = {"randutv_residual": res, "randutv_orth_u": orth_u, "randutv_orth_v": orth_v,
-                    "t_lower_exact_zero": lower_zero, "e_k_over_sigma_k+1": ratios}
+                    "t_lower_exact_zero": lower_zero, "e_k_over_sigma_k+1": ratios,
+                    "max_ratio": max(ratios.values()) if ratios else None, "boundaries": len(ratios),
+                    "on_target": sum(1 for v in ratios.values() if v <= 1.1)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
