@@ -59,3 +59,14 @@ def test_measured_peaks_fall_back_when_absent(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, src = bench.measured_peaks()
     assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
+
+
+def test_boundary_ratios_use_the_spectral_norm():
+    """bench's e_k / sigma_{k+1} helper (power iteration) against numpy's 2-norm of the trailing blocks."""
+    torch = __import__("pytest").importorskip("torch")
+    rng = np.random.default_rng(3)
+    T = np.triu(rng.standard_normal((96, 96))) * np.logspace(0, -3, 96)
+    s = np.logspace(0, -3, 96)
+    r = bench._boundary_ratios(torch, torch.from_numpy(T), s, 32, [32, 64])
+    for k in (32, 64):
+        assert abs(r[str(k)] - np.linalg.norm(T[k:, k:], 2) / s[k]) <= 1e-4 * r[str(k)]
