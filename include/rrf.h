@@ -14,7 +14,10 @@
  *  - Matrices are column-major FP64 with an explicit leading dimension (ld >= rows).  Unless an entry
  *    point says "host", every matrix pointer is a DEVICE pointer owned by the caller.
  *  - A is read-only.  U, T and V are written completely (every entry of the m x m, m x n and n x n
- *    blocks).  The output buffers must not alias A or each other.
+ *    blocks).  The output buffers must not alias A or each other, with one exception: rrf_randutv
+ *    (device and host forms) accepts T == A with ldt == lda and then factors in place (A is
+ *    overwritten by T); so does rrf_powerurv for m < n, which consumes A into A^T first.  For m >= n
+ *    rrf_powerurv rejects T == A (it reads A after writing T).
  *  - The Gaussian matrices the methods draw (randn in Algorithms 1 and 3) come from the
  *    counter-based Philox-4x32-10 stream (Salmon et al., SC'11) with key = (seed lo32, seed hi32).
  *    Block t of a draw uses counter (t lo32, t hi32, step, tag) and yields column-major elements

@@ -228,16 +228,17 @@ rrf_status factor_wide(WsFn wsfn, RunFn run, int64_t m, int64_t n, const double*
     set_arg_error(14);
     return RRF_INVALID_ARG;
   }
-  // The tall call checks q and the options; with no workspace it stops before enqueuing anything.
-  const rrf_status v = run(n, m, A, n, b, q, V, ldv, T, n, U, ldu, seed, workspace, 0, opts, stream_);
-  if (v != RRF_WORKSPACE_TOO_SMALL && v != RRF_OK) return v;
-  clear_arg_error();
   const size_t inner = wsfn(n, m, b, opts);
-  if (ws_bytes < wide_workspace(wsfn, m, n, b, opts)) { set_arg_error(15); return RRF_WORKSPACE_TOO_SMALL; }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   double* At = reinterpret_cast<double*>(reinterpret_cast<char*>(workspace) + align_up(inner, 256));
   double* Tt = reinterpret_cast<double*>(reinterpret_cast<char*>(At) +
                                          align_up(sizeof(double) * (size_t)m * (size_t)n, 256));
+  // The tall call checks q and the options on the buffers it will get; with no workspace it stops before
+  // enqueuing anything (nothing is dereferenced).
+  const rrf_status v = run(n, m, At, n, b, q, V, ldv, Tt, n, U, ldu, seed, workspace, 0, opts, stream_);
+  if (v != RRF_WORKSPACE_TOO_SMALL && v != RRF_OK) return v;
+  clear_arg_error();
+  if (ws_bytes < wide_workspace(wsfn, m, n, b, opts)) { set_arg_error(15); return RRF_WORKSPACE_TOO_SMALL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   RRF_CUDA_TRY(transpose_matrix(m, n, A, lda, At, n, s));
   // A^T (n x m, tall) = U' T' V'^T: U' (n x n) lands in V, V' (m x m) in U.
   const rrf_status r = run(n, m, At, n, b, q, V, ldv, Tt, n, U, ldu, seed, workspace, inner, opts, stream_);

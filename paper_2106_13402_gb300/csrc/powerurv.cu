@@ -144,6 +144,7 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   if (ldt < m) { set_arg_error(10); return RRF_INVALID_ARG; }
   if (V == nullptr) { set_arg_error(11); return RRF_INVALID_ARG; }
   if (ldv < n) { set_arg_error(12); return RRF_INVALID_ARG; }
+  if (T == A) { set_arg_error(9); return RRF_INVALID_ARG; }  // A is read after T is written
   if (opts != nullptr && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->q_per_block != nullptr ||
                           opts->q_policy != RRF_Q_FIXED || opts->gemm_mode < RRF_GEMM_AUTO ||
                           opts->gemm_mode > RRF_GEMM_EMULATED || opts->oversample != 0 ||

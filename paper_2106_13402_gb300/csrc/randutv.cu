@@ -303,7 +303,7 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
   if (U == nullptr) { set_arg_error(7); return RRF_INVALID_ARG; }
   if (ldu < m) { set_arg_error(8); return RRF_INVALID_ARG; }
   if (T == nullptr) { set_arg_error(9); return RRF_INVALID_ARG; }
-  if (ldt < m) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (ldt < m || (T == A && ldt != lda)) { set_arg_error(10); return RRF_INVALID_ARG; }
   if (V == nullptr) { set_arg_error(11); return RRF_INVALID_ARG; }
   if (ldv < n) { set_arg_error(12); return RRF_INVALID_ARG; }
   if (opts != nullptr) {
@@ -377,8 +377,8 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
 
   RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
   RRF_CUDA_TRY(check_finite(m, n, A, lda, &w.hdr->status, s));
-  // T = A; U = I_m; V = I_n.
-  RRF_CUDA_TRY(copy_matrix(m, n, A, lda, T, ldt, s));
+  // T = A (nothing to copy when factoring in place); U = I_m; V = I_n.
+  if (T != A) RRF_CUDA_TRY(copy_matrix(m, n, A, lda, T, ldt, s));
   RRF_CUDA_TRY(fill_identity(m, m, U, ldu, s));
   RRF_CUDA_TRY(fill_identity(n, n, V, ldv, s));
 

@@ -44,9 +44,14 @@ def test_status_strings_and_version(L):
         assert L.rrf_status_string(code).decode() == name
 
 
+def _fakes():
+    # distinct addresses that are never dereferenced: validation fails first
+    return [ctypes.c_void_p(0x10000 * k) for k in (1, 2, 3, 4)]
+
+
 def _call(L, name, m, n, lda, b, q, ldu, ldt, ldv, ws=1 << 20, nullA=False):
-    fake = ctypes.c_void_p(0x10000)  # never dereferenced: validation fails first
-    return getattr(L, name)(m, n, None if nullA else fake, lda, b, q, fake, ldu, fake, ldt, fake, ldv, 1,
+    fa, fu, ft, fv = _fakes()
+    return getattr(L, name)(m, n, None if nullA else fa, lda, b, q, fu, ldu, ft, ldt, fv, ldv, 1,
                             ctypes.c_void_p(0x100000), ws, None, None)
 
 
@@ -87,10 +92,11 @@ def test_oversample_option_validation(L):
     """randUTV_boosted (Algorithm 2) is selected by opts.oversample = p > 0: 1 <= b + p <= 256, FP64 sketch,
     no re-orthonormalization, fixed q; powerURV has no oversampling."""
     fake = ctypes.c_void_p(0x10000)
+    fa, fu, ft, fv = _fakes()
 
     def call(name, b, **kw):
         o = rrf.make_opts(**kw)
-        return getattr(L, name)(40, 30, fake, 40, b, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000),
+        return getattr(L, name)(40, 30, fa, 40, b, 1, fu, 40, ft, 40, fv, 30, 1, ctypes.c_void_p(0x100000),
                                 1 << 20, ctypes.byref(o), None)
 
     for kw in (dict(oversample=-1), dict(oversample=129), dict(oversample=8, sketch_prec=rrf.SKETCH_BF16),
@@ -133,10 +139,28 @@ def test_frobenius_option_validation(L):
                              1 << 20, ctypes.byref(o), None) == rrf.RRF_INVALID_ARG
         assert L.rrf_last_arg_error() == 16
     o = rrf.make_opts(frob_tol=1e-3)
-    assert L.rrf_powerurv(40, 30, fake, 40, 16, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000),
+    fa, fu, ft, fv = _fakes()
+    assert L.rrf_powerurv(40, 30, fa, 40, 16, 1, fu, 40, ft, 40, fv, 30, 1, ctypes.c_void_p(0x100000),
                           1 << 20, ctypes.byref(o), None) == rrf.RRF_UNSUPPORTED
     with pytest.raises(ValueError):
         rrf.make_opts(track_frob=True)
+
+
+def test_in_place_rules(L):
+    """T == A: randUTV factors in place when ldt == lda; powerURV (m >= n) reads A after writing T."""
+    fa, fu, ft, fv = _fakes()
+    ws = ctypes.c_void_p(0x100000)
+    assert L.rrf_randutv(40, 30, fa, 40, 16, 1, fu, 40, fa, 41, fv, 30, 1, ws, 1 << 20, None, None) == \
+        rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 10
+    assert L.rrf_randutv(40, 30, fa, 40, 16, 1, fu, 40, fa, 40, fv, 30, 1, ws, 16, None, None) == \
+        rrf.RRF_WORKSPACE_TOO_SMALL
+    assert L.rrf_powerurv(40, 30, fa, 40, 16, 1, fu, 40, fa, 40, fv, 30, 1, ws, 1 << 20, None, None) == \
+        rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 9
+    # wide powerURV consumes A into A^T first: in place is accepted (stops here at the workspace size)
+    assert L.rrf_powerurv(30, 40, fa, 30, 16, 1, fu, 30, fa, 30, fv, 40, 1, ws, 16, None, None) == \
+        rrf.RRF_WORKSPACE_TOO_SMALL
 
 
 def test_small_entry_point_validation(L):

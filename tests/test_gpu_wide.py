@@ -1,7 +1,8 @@
 """GPU factorizations of wide matrices (m < n) through the transpose (Sec. 1.3 footnote): the call factors
 A^T = U' T' V'^T and returns U = V', T = T'^T (lower trapezoidal), V = U'.  The result must equal, bit for
 bit, the tall call on A^T rearranged that way (same kernels on the same data), factor A exactly, and match
-the FP64 oracle run on A^T (|diag T| within 1e-10 relative, as for tall inputs).
+the FP64 oracle run on A^T (|diag T| within 1e-10 relative, as for tall inputs).  Also the in-place form
+(T == A): bit for bit the out-of-place result.
 """
 import numpy as np
 import pytest
@@ -76,3 +77,16 @@ def test_wide_host_entry_point_matches_device():
     Ud, Td, Vd = (host(x) for x in rrf.randutv(dev(A), 32, 1, seed=4))
     Uh, Th, Vh = rrf.randutv_host(A, 32, 1, seed=4)
     assert np.array_equal(Ud, Uh) and np.array_equal(Td, Th) and np.array_equal(Vd, Vh)
+
+
+@pytest.mark.parametrize("m,n,p", [(200, 160, 0), (90, 300, 32)])
+def test_randutv_in_place_equals_out_of_place(m, n, p):
+    rng = np.random.default_rng(m)
+    A = np.asfortranarray(rng.standard_normal((m, n)))
+    opts = rrf.make_opts(oversample=p)
+    U1, T1, V1 = (host(x) for x in rrf.randutv(dev(A), 32, 1, seed=5, opts=opts))
+    Ad = dev(A)
+    out = (rrf.fortran_empty(m, m, Ad.device), Ad, rrf.fortran_empty(n, n, Ad.device))
+    U2, T2, V2 = rrf.randutv(Ad, 32, 1, seed=5, opts=opts, out=out)
+    assert T2.data_ptr() == Ad.data_ptr()
+    assert np.array_equal(host(U2), U1) and np.array_equal(host(T2), T1) and np.array_equal(host(V2), V1)
