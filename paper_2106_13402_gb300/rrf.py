@@ -367,6 +367,21 @@ def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, 
     return C
 
 
+def low_rank(U, T, V, k: int, stream=None, emulated: bool = False):
+    """Rank-k approximation from a (partial) randUTV factorization, Sec. 4.1: A_k = U(:, :k) (T(:k, :) V^T),
+    i.e. U1 (T11 V1^T + T12 V2^T); the error ||A - A_k|| equals ||T(k:, k:)|| in the 2- and Frobenius norms.
+    Both products run in the library's GEMM (DFMA, or emulated on the tensor cores)."""
+    m, n = T.shape
+    if not 0 <= k <= min(m, n):
+        raise ValueError(f"k = {k} outside [0, {min(m, n)}]")
+    if k == 0:
+        Z = fortran_empty(m, n, T.device)
+        Z.zero_()
+        return Z
+    X = gemm("N", "T", T[:k, :], V, stream=stream, emulated=emulated)     # T(:k, :) V^T, k x n
+    return gemm("N", "N", U[:, :k], X, stream=stream, emulated=emulated)  # U(:, :k) X, m x n
+
+
 def gemm_bf16(A, B, alpha: float = 1.0, stream=None):
     """D = alpha A B^T (FP64, column-major) from BF16 tensors A (m x k) and B (n x k) with contiguous rows
     (row stride a multiple of 8 elements), FP32 accumulation on the tensor cores."""

@@ -95,3 +95,21 @@ def test_tolerance_above_norm_does_no_step():
     assert np.array_equal(T, A)
     assert np.array_equal(U, np.eye(100)) and np.array_equal(V, np.eye(80))
     assert abs(fr[0] - np.linalg.norm(A)) <= 1e-13 * np.linalg.norm(A)
+
+
+def test_low_rank_approximation_error_is_the_trailing_norm():
+    """A_k = U1 (T11 V1^T + T12 V2^T) from the stopped factorization (Sec. 4.1): ||A - A_k||_F = e_done and
+    ||A - A_k||_2 = ||T(k:, k:)||_2."""
+    A, s = testmats.make_matrix(300, 250, "exp8", 3, 4)
+    eo = oracle_e(A, 32, 1, 11)
+    tol = np.sqrt(eo[2] * eo[3])
+    o = rrf.make_opts(frob_tol=tol, track_frob=True, steps=8)
+    U, T, V = rrf.randutv(dev(A), 32, 1, seed=11, opts=o)
+    k = rrf.opts_steps_done(o) * 32
+    assert k == 96
+    Ak = host(rrf.low_rank(U, T, V, k))
+    Th = host(T)
+    err = A - Ak
+    assert abs(np.linalg.norm(err) - eo[3]) <= 1e-10 * eo[3] + 1e-12 * np.linalg.norm(A)
+    t2 = np.linalg.norm(Th[k:, k:], 2)
+    assert abs(np.linalg.norm(err, 2) - t2) <= 1e-10 * t2 + 1e-12 * np.linalg.norm(A)
