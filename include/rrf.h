@@ -258,6 +258,17 @@ RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
 RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                           double* Vs, int64_t ldv, void* workspace, size_t ws_bytes, void* stream);
 
+/* Rank-k approximation from a (partial) randUTV factorization (Sec. 4.1): Ak = U(:, 1:k) (T(1:k, :) V^T),
+ * i.e. U1 (T11 V1^T + T12 V2^T), whose error ||A - Ak|| equals ||T(k+1:m, k+1:n)|| in the 2- and Frobenius
+ * norms.  U is m x m (its first k columns are read), T m x n, V n x n, Ak m x n (ldak >= m, written
+ * completely; must not alias the inputs); 0 <= k <= min(m, n) (k = 0 gives Ak = 0).  Both products run on
+ * the FP64 DFMA GEMM.  Workspace: rrf_low_rank_workspace(m, n, k) bytes (the k x n product T(1:k, :) V^T
+ * and split-K partial sums), 256-byte aligned. */
+RRF_API size_t rrf_low_rank_workspace(int64_t m, int64_t n, int64_t k);
+RRF_API rrf_status rrf_low_rank(int64_t m, int64_t n, int64_t k, const double* U, int64_t ldu, const double* T,
+                                int64_t ldt, const double* V, int64_t ldv, double* Ak, int64_t ldak, void* workspace,
+                                size_t ws_bytes, void* stream);
+
 /* Householder panel QR that allocates nothing and takes no workspace.  The paper has no counterpart:
  * this serves callers that cannot give the library device memory for scratch -- code running under
  * a memory manager that owns the whole device, or loops that must not allocate once running.

@@ -110,6 +110,64 @@ extern "C" rrf_status rrf_gemm(char transa, char transb, int64_t m, int64_t n, i
   return RRF_OK;
 }
 
+// ---- rank-k approximation of a (partial) randUTV factorization (Sec. 4.1) ------------------------------
+namespace {
+void low_rank_descs(int64_t m, int64_t n, int64_t k, const double* U, int64_t ldu, const double* T, int64_t ldt,
+                    const double* V, int64_t ldv, double* X, double* Ak, int64_t ldak, GemmDesc* g) {
+  g[0].M = k; g[0].N = n; g[0].K = n;  // X = T(0:k, :) V^T
+  g[0].A = T; g[0].lda = ldt; g[0].ta = 0;
+  g[0].B = V; g[0].ldb = ldv; g[0].tb = 1;
+  g[0].C = X; g[0].ldc = std::max<int64_t>(k, 1);
+  g[1].M = m; g[1].N = n; g[1].K = k;  // Ak = U(:, 0:k) X
+  g[1].A = U; g[1].lda = ldu; g[1].ta = 0;
+  g[1].B = X; g[1].ldb = std::max<int64_t>(k, 1); g[1].tb = 0;
+  g[1].C = Ak; g[1].ldc = ldak;
+}
+}  // namespace
+
+extern "C" size_t rrf_low_rank_workspace(int64_t m, int64_t n, int64_t k) {
+  if (m < 1 || n < 1 || k < 0) return 0;
+  GemmDesc g[2];
+  low_rank_descs(m, n, k, nullptr, m, nullptr, m, nullptr, n, nullptr, nullptr, m, g);
+  return align_up(sizeof(double) * (size_t)std::max<int64_t>(k, 1) * (size_t)n, 256) +
+         std::max(gemm_scratch_bytes(&g[0], 1), gemm_scratch_bytes(&g[1], 1));
+}
+
+extern "C" rrf_status rrf_low_rank(int64_t m, int64_t n, int64_t k, const double* U, int64_t ldu, const double* T,
+                                   int64_t ldt, const double* V, int64_t ldv, double* Ak, int64_t ldak,
+                                   void* workspace, size_t ws_bytes, void* stream) {
+  clear_arg_error();
+  if (m < 1) { set_arg_error(1); return RRF_INVALID_ARG; }
+  if (n < 1) { set_arg_error(2); return RRF_INVALID_ARG; }
+  if (k < 0 || k > std::min(m, n)) { set_arg_error(3); return RRF_INVALID_ARG; }
+  if (U == nullptr) { set_arg_error(4); return RRF_INVALID_ARG; }
+  if (ldu < m) { set_arg_error(5); return RRF_INVALID_ARG; }
+  if (T == nullptr) { set_arg_error(6); return RRF_INVALID_ARG; }
+  if (ldt < m) { set_arg_error(7); return RRF_INVALID_ARG; }
+  if (V == nullptr) { set_arg_error(8); return RRF_INVALID_ARG; }
+  if (ldv < n) { set_arg_error(9); return RRF_INVALID_ARG; }
+  if (Ak == nullptr) { set_arg_error(10); return RRF_INVALID_ARG; }
+  if (ldak < m) { set_arg_error(11); return RRF_INVALID_ARG; }
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
+    set_arg_error(12);
+    return RRF_INVALID_ARG;
+  }
+  if (ws_bytes < rrf_low_rank_workspace(m, n, k)) { set_arg_error(13); return RRF_WORKSPACE_TOO_SMALL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    RRF_CUDA_TRY(zero_matrix(m, n, Ak, ldak, s));
+    return RRF_OK;
+  }
+  double* X = reinterpret_cast<double*>(workspace);
+  const size_t xb = align_up(sizeof(double) * (size_t)k * (size_t)n, 256);
+  double* scratch = reinterpret_cast<double*>(reinterpret_cast<char*>(workspace) + xb);
+  GemmDesc g[2];
+  low_rank_descs(m, n, k, U, ldu, T, ldt, V, ldv, X, Ak, ldak, g);
+  RRF_CUDA_TRY(gemm_f64(&g[0], 1, scratch, ws_bytes - xb, s));
+  RRF_CUDA_TRY(gemm_f64(&g[1], 1, scratch, ws_bytes - xb, s));
+  return RRF_OK;
+}
+
 extern "C" size_t rrf_gemm_bf16_workspace(int64_t m, int64_t n, int64_t k) {
   if (m < 1 || n < 1) return kHeaderBytes;
   return kHeaderBytes + tc_part_bytes(m, n, k);

@@ -30,7 +30,7 @@ EXPORTED = [
     "rrf_gemm_bf16_workspace", "rrf_gemm_bf16", "rrf_batch_plan_create", "rrf_batch_plan_workspace",
     "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
     "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
-    "rrf_gemm_emulated", "rrf_gemm_profile_emulated",
+    "rrf_gemm_emulated", "rrf_gemm_profile_emulated", "rrf_low_rank_workspace", "rrf_low_rank",
 ]
 
 
@@ -148,6 +148,10 @@ def lib():
             L.rrf_gemm_profile_emulated.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [
                 ctypes.POINTER(ctypes.c_int64)]
             L.rrf_gemm_profile_emulated.restype = ctypes.c_int
+            L.rrf_low_rank_workspace.argtypes = [_i64, _i64, _i64]
+            L.rrf_low_rank_workspace.restype = _sz
+            L.rrf_low_rank.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]
+            L.rrf_low_rank.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -367,19 +371,18 @@ def gemm(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, 
     return C
 
 
-def low_rank(U, T, V, k: int, stream=None, emulated: bool = False):
-    """Rank-k approximation from a (partial) randUTV factorization, Sec. 4.1: A_k = U(:, :k) (T(:k, :) V^T),
-    i.e. U1 (T11 V1^T + T12 V2^T); the error ||A - A_k|| equals ||T(k:, k:)|| in the 2- and Frobenius norms.
-    Both products run in the library's GEMM (DFMA, or emulated on the tensor cores)."""
+def low_rank(U, T, V, k: int, stream=None):
+    """rrf_low_rank: the rank-k approximation A_k = U(:, :k) (T(:k, :) V^T) of a (partial) randUTV
+    factorization (Sec. 4.1); ||A - A_k|| equals ||T(k:, k:)|| in the 2- and Frobenius norms."""
+    L = lib()
     m, n = T.shape
-    if not 0 <= k <= min(m, n):
-        raise ValueError(f"k = {k} outside [0, {min(m, n)}]")
-    if k == 0:
-        Z = fortran_empty(m, n, T.device)
-        Z.zero_()
-        return Z
-    X = gemm("N", "T", T[:k, :], V, stream=stream, emulated=emulated)     # T(:k, :) V^T, k x n
-    return gemm("N", "N", U[:, :k], X, stream=stream, emulated=emulated)  # U(:, :k) X, m x n
+    U, T, V = as_fortran(U), as_fortran(T), as_fortran(V)
+    Ak = fortran_empty(m, n, T.device)
+    ws = workspace(L.rrf_low_rank_workspace(m, n, k), T.device)
+    st = L.rrf_low_rank(m, n, k, _vp(U.data_ptr()), _ld(U), _vp(T.data_ptr()), _ld(T), _vp(V.data_ptr()), _ld(V),
+                        _vp(Ak.data_ptr()), _ld(Ak), _vp(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(st, "rrf_low_rank")
+    return Ak
 
 
 def gemm_bf16(A, B, alpha: float = 1.0, stream=None):

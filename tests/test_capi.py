@@ -163,6 +163,20 @@ def test_in_place_rules(L):
         rrf.RRF_WORKSPACE_TOO_SMALL
 
 
+def test_low_rank_validation(L):
+    fa, fu, ft, fv = _fakes()
+    ws = ctypes.c_void_p(0x100000)
+    assert L.rrf_low_rank(40, 30, 31, fu, 40, ft, 40, fv, 30, fa, 40, ws, 1 << 20, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 3
+    assert L.rrf_low_rank(40, 30, 8, fu, 39, ft, 40, fv, 30, fa, 40, ws, 1 << 20, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 5
+    assert L.rrf_low_rank(40, 30, 8, fu, 40, ft, 40, fv, 30, fa, 39, ws, 1 << 20, None) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 11
+    assert L.rrf_low_rank(40, 30, 8, fu, 40, ft, 40, fv, 30, fa, 40, ws, 16, None) == rrf.RRF_WORKSPACE_TOO_SMALL
+    assert L.rrf_last_arg_error() == 13
+    assert L.rrf_low_rank_workspace(40, 30, 8) >= 8 * 30 * 8
+
+
 def test_small_entry_point_validation(L):
     fake = ctypes.c_void_p(0x10000)
     assert L.rrf_gemm(b"X", b"N", 2, 2, 2, 1.0, fake, 2, fake, 2, 0.0, fake, 2, None, 0, None) == rrf.RRF_INVALID_ARG
