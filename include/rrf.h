@@ -100,7 +100,9 @@ typedef struct rrf_opts {
   double frob_tol;   /* > 0: early termination by the Frobenius recurrence of Sec. 4.1 (see rrf_randutv); 0 off */
   double* frob_out;  /* optional HOST array [ceil(n/b) + 1]: e_0 = ||A||_F, e_1, ..., e_steps (recurrence)   */
   int* steps_out;    /* optional HOST int: the number of steps performed                                 */
-  int reserved[2];   /* must be zero */
+  int resume_steps;  /* s0 > 0: U, T, V already hold a factorization stopped after s0 steps (e.g. by
+                        frob_tol); continue from step s0 + 1 (see rrf_randutv).  0: start from A.      */
+  int reserved[1];   /* must be zero */
 } rrf_opts;
 
 /* ------------------------------------------------------------------------------------------------
@@ -137,6 +139,13 @@ typedef struct rrf_opts {
  * tolerance synchronizes the stream once per step, so such a call cannot be captured in a CUDA graph.
  * frob_out receives e_0 .. e_done (written before return: with frob_tol = 0 the call synchronizes once
  * at the end to fill it); steps_out (any mode) receives the number of steps done.
+ *
+ * Resume (checkpoint at a block boundary: the state after step s0 is (U, T, V, s0), Sec. 4.1).  With
+ * opts->resume_steps = s0 > 0 the call does not read A: it takes U, T, V as a factorization of A after s0
+ * steps (as left by a call that stopped there) and runs steps s0 + 1, ...; step i still draws the Gaussian
+ * of step i, so stopping and resuming gives the same U, T, V bit for bit as one uninterrupted call.  With
+ * the Frobenius options, e_s0 is computed directly from T(s0 b:, s0 b:) and frob_out[0 .. s0 - 1] are NaN.
+ * Requires m >= n, the randUTV_basic sample (oversample = 0) and fixed q.
  * ---------------------------------------------------------------------------------------------- */
 RRF_API size_t rrf_randutv_workspace(int64_t m, int64_t n, int64_t b, const rrf_opts* opts);
 RRF_API rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q,

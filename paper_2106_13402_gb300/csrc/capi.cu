@@ -286,6 +286,7 @@ rrf_status factor_wide(WsFn wsfn, RunFn run, int64_t m, int64_t n, const double*
     set_arg_error(14);
     return RRF_INVALID_ARG;
   }
+  if (opts != nullptr && opts->resume_steps != 0) { set_arg_error(16); return RRF_UNSUPPORTED; }  // state is A^T's
   const size_t inner = wsfn(n, m, b, opts);
   double* At = reinterpret_cast<double*>(reinterpret_cast<char*>(workspace) + align_up(inner, 256));
   double* Tt = reinterpret_cast<double*>(reinterpret_cast<char*>(At) +

@@ -148,7 +148,8 @@ extern "C" rrf_status rrf_powerurv(int64_t m, int64_t n, const double* A, int64_
   if (opts != nullptr && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->q_per_block != nullptr ||
                           opts->q_policy != RRF_Q_FIXED || opts->gemm_mode < RRF_GEMM_AUTO ||
                           opts->gemm_mode > RRF_GEMM_EMULATED || opts->oversample != 0 ||
-                          opts->frob_tol != 0.0 || opts->frob_out != nullptr || opts->steps_out != nullptr)) {
+                          opts->frob_tol != 0.0 || opts->frob_out != nullptr || opts->steps_out != nullptr ||
+                          opts->resume_steps != 0)) {
     set_arg_error(16);
     return RRF_UNSUPPORTED;
   }

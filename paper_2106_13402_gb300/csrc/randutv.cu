@@ -312,8 +312,13 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
     }
     if (opts->q_policy != RRF_Q_FIXED && opts->q_policy != RRF_Q_LEARNED) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->q_policy == RRF_Q_LEARNED && opts->q_per_block != nullptr) { set_arg_error(16); return RRF_INVALID_ARG; }
-    for (int i = 0; i < 2; ++i)
-      if (opts->reserved[i] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->reserved[0] != 0) { set_arg_error(16); return RRF_INVALID_ARG; }
+    const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
+    if (opts->resume_steps < 0 || opts->resume_steps > steps) { set_arg_error(16); return RRF_INVALID_ARG; }
+    if (opts->resume_steps > 0 && (m < n || opts->oversample != 0 || opts->q_policy != RRF_Q_FIXED)) {
+      set_arg_error(16);
+      return RRF_INVALID_ARG;
+    }
     if (opts->oversample < 0 || b + opts->oversample > 256) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (!(opts->frob_tol >= 0.0) || std::isinf(opts->frob_tol)) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->oversample > 0 && (opts->sketch_prec != RRF_SKETCH_FP64 || opts->reorth != 0 ||
@@ -323,7 +328,6 @@ rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_
     }
     if (opts->gemm_mode < RRF_GEMM_AUTO || opts->gemm_mode > RRF_GEMM_EMULATED) { set_arg_error(16); return RRF_INVALID_ARG; }
     if (opts->q_per_block != nullptr) {
-      const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
       for (int64_t i = 0; i < steps; ++i)
         if (opts->q_per_block[i] < 0 || opts->q_per_block[i] > 16) { set_arg_error(16); return RRF_INVALID_ARG; }
     }
@@ -376,11 +380,15 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   if (ar.overflow) return RRF_WORKSPACE_TOO_SMALL;
 
   RRF_CUDA_TRY(cudaMemsetAsync(w.hdr, 0, kHeaderBytes, s));
-  RRF_CUDA_TRY(check_finite(m, n, A, lda, &w.hdr->status, s));
-  // T = A (nothing to copy when factoring in place); U = I_m; V = I_n.
-  if (T != A) RRF_CUDA_TRY(copy_matrix(m, n, A, lda, T, ldt, s));
-  RRF_CUDA_TRY(fill_identity(m, m, U, ldu, s));
-  RRF_CUDA_TRY(fill_identity(n, n, V, ldv, s));
+  // Resume: U, T, V already hold the factorization after `start` steps; A is not read.
+  const int64_t start = opts != nullptr ? opts->resume_steps : 0;
+  if (start == 0) {
+    RRF_CUDA_TRY(check_finite(m, n, A, lda, &w.hdr->status, s));
+    // T = A (nothing to copy when factoring in place); U = I_m; V = I_n.
+    if (T != A) RRF_CUDA_TRY(copy_matrix(m, n, A, lda, T, ldt, s));
+    RRF_CUDA_TRY(fill_identity(m, m, U, ldu, s));
+    RRF_CUDA_TRY(fill_identity(n, n, V, ldv, s));
+  }
 
   const int64_t steps = std::min((m + b - 1) / b, (n + b - 1) / b);
   const bool learned = opts != nullptr && opts->q_policy == RRF_Q_LEARNED;
@@ -396,12 +404,14 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
     return e;
   };
   bool stop = false;
-  int64_t done = 0;
-  if (frob) {
-    RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, s));
-    if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(0, &stop));
+  int64_t done = start;
+  if (frob) {  // e_start from its definition: ||A||_F, or the trailing block's norm when resuming
+    const int64_t o = b * start;
+    if (start == 0) RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, s));
+    else RRF_CUDA_TRY(frob_step(m - o, n - o, T + o + o * ldt, ldt, w.fpart, w.e2, start, true, s));
+    if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(start, &stop));
   }
-  for (int64_t i = 1; i <= steps && !stop; ++i) {
+  for (int64_t i = start + 1; i <= steps && !stop; ++i) {
     const int64_t o = b * (i - 1);
     const int64_t r = m - o, c = n - o;
     double* T22 = T + o + o * ldt;
@@ -546,7 +556,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
     std::vector<double> e2((size_t)done + 1);
     RRF_CUDA_TRY(cudaMemcpyAsync(e2.data(), w.e2, e2.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     RRF_CUDA_TRY(cudaStreamSynchronize(s));
-    for (size_t j = 0; j < e2.size(); ++j) opts->frob_out[j] = std::sqrt(e2[j]);
+    for (size_t j = 0; j < e2.size(); ++j) opts->frob_out[j] = (int64_t)j < start ? NAN : std::sqrt(e2[j]);
   }
   return RRF_OK;
 }

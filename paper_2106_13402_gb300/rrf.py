@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
                 ("features_out", ctypes.POINTER(ctypes.c_float)), ("gemm_mode", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("frob_tol", ctypes.c_double),
                 ("frob_out", ctypes.POINTER(ctypes.c_double)), ("steps_out", ctypes.POINTER(ctypes.c_int)),
-                ("reserved", ctypes.c_int * 2)]
+                ("resume_steps", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 Q_FIXED, Q_LEARNED = 0, 1
@@ -197,12 +197,13 @@ def _check(st: int, what: str):
 
 def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=None, q_policy: int = Q_FIXED,
               mlp_params=None, steps: int = 0, gemm_mode: int = GEMM_AUTO, oversample: int = 0,
-              frob_tol: float = 0.0, track_frob: bool = False):
+              frob_tol: float = 0.0, track_frob: bool = False, resume_steps: int = 0):
     """rrf_opts.  With q_policy=Q_LEARNED, pass `steps` (= ceil(n/b)) to receive per-step q and features in
     opts.q_used / opts.features after the call; mlp_params is a CUDA float16 tensor of rrf_mlp_param_count
     values (None: features only, q stays fixed).  oversample = p > 0 selects randUTV_boosted (Algorithm 2).
     frob_tol > 0 stops at the first step whose trailing Frobenius norm e_i <= frob_tol (Sec. 4.1);
-    with track_frob (needs `steps`) opts_frob(o) returns e_0 .. e_done and opts_steps_done(o) the count."""
+    with track_frob (needs `steps`) opts_frob(o) returns e_0 .. e_done and opts_steps_done(o) the count.
+    resume_steps = s0 > 0 continues a factorization stopped after s0 steps (U, T, V passed as `out`)."""
     o = Opts()
     o.sketch_prec = int(sketch_prec)
     o.reorth = 1 if reorth else 0
@@ -210,6 +211,7 @@ def make_opts(sketch_prec: int = SKETCH_FP64, reorth: bool = False, q_per_block=
     o.gemm_mode = int(gemm_mode)
     o.oversample = int(oversample)
     o.frob_tol = float(frob_tol)
+    o.resume_steps = int(resume_steps)
     keep = []
     if track_frob or frob_tol > 0:
         sd = ctypes.c_int(-1)

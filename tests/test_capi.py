@@ -105,7 +105,7 @@ def test_oversample_option_validation(L):
         assert L.rrf_last_arg_error() == 16
     assert call("rrf_powerurv", 16, oversample=8) == rrf.RRF_UNSUPPORTED
     o = rrf.make_opts(oversample=64)
-    o.reserved[1] = 1
+    o.reserved[0] = 1
     assert L.rrf_randutv(40, 30, fake, 40, 16, 1, fake, 40, fake, 40, fake, 30, 1, ctypes.c_void_p(0x100000), 1 << 20,
                          ctypes.byref(o), None) == rrf.RRF_INVALID_ARG
     # the boosted workspace holds the b + p column sample and its SVD
@@ -160,6 +160,26 @@ def test_in_place_rules(L):
     assert L.rrf_last_arg_error() == 9
     # wide powerURV consumes A into A^T first: in place is accepted (stops here at the workspace size)
     assert L.rrf_powerurv(30, 40, fa, 30, 16, 1, fu, 30, fa, 30, fv, 40, 1, ws, 16, None, None) == \
+        rrf.RRF_WORKSPACE_TOO_SMALL
+
+
+def test_resume_option_validation(L):
+    """resume_steps: 0 <= s0 <= ceil(n / b), tall randUTV_basic with fixed q only."""
+    fa, fu, ft, fv = _fakes()
+    ws = ctypes.c_void_p(0x100000)
+
+    def call(name, m, n, **kw):
+        o = rrf.make_opts(**kw)
+        return getattr(L, name)(m, n, fa, m, 16, 1, fu, m, ft, m, fv, n, 1, ws, 1 << 20, ctypes.byref(o), None)
+
+    for kw in (dict(resume_steps=-1), dict(resume_steps=3), dict(resume_steps=1, oversample=8),
+               dict(resume_steps=1, q_policy=rrf.Q_LEARNED)):
+        assert call("rrf_randutv", 40, 30, **kw) == rrf.RRF_INVALID_ARG, kw
+        assert L.rrf_last_arg_error() == 16
+    assert call("rrf_randutv", 30, 40, resume_steps=1) == rrf.RRF_UNSUPPORTED
+    assert call("rrf_powerurv", 40, 30, resume_steps=1) == rrf.RRF_UNSUPPORTED
+    o = rrf.make_opts(resume_steps=2)
+    assert L.rrf_randutv(40, 30, fa, 40, 16, 1, fu, 40, ft, 40, fv, 30, 1, ws, 16, ctypes.byref(o), None) == \
         rrf.RRF_WORKSPACE_TOO_SMALL
 
 

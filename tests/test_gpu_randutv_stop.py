@@ -6,6 +6,7 @@ oracle's complete factorization gives every e_i as ||To(ib:, ib:)||_F.  Toleranc
 within 1e-12 ||A||_F^2 of the oracle's (its cancellation error is of order eps ||A||_F^2 per step); a
 stopped factorization keeps A = U T V^T and orthogonality to 1e-12, its first ib columns upper trapezoidal
 with diagonal b x b blocks (exact zeros), and ||T(ib:, ib:)||_F within 1e-10 relative of the oracle's e_i.
+A stopped factorization resumed from its step count equals the uninterrupted call bit for bit.
 """
 import numpy as np
 import pytest
@@ -113,3 +114,25 @@ def test_low_rank_approximation_error_is_the_trailing_norm():
     assert abs(np.linalg.norm(err) - eo[3]) <= 1e-10 * eo[3] + 1e-12 * np.linalg.norm(A)
     t2 = np.linalg.norm(Th[k:, k:], 2)
     assert abs(np.linalg.norm(err, 2) - t2) <= 1e-10 * t2 + 1e-12 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("m,n,b,q,prof", [(300, 250, 32, 1, "exp8"), (257, 129, 16, 2, "fast")])
+def test_stop_then_resume_equals_one_call(m, n, b, q, prof):
+    """A factorization stopped by the tolerance and resumed (opts.resume_steps) gives the uninterrupted
+    call's U, T, V bit for bit; A is not read when resuming."""
+    A, s = testmats.make_matrix(m, n, prof, 3, 4)
+    steps = -(-n // b)
+    Uf, Tf, Vf = (host(x) for x in rrf.randutv(dev(A), b, q, seed=5))
+    eo = oracle_e(A, b, q, 5)
+    o1 = rrf.make_opts(frob_tol=np.sqrt(eo[2] * eo[3]), track_frob=True, steps=steps)
+    U, T, V = rrf.randutv(dev(A), b, q, seed=5, opts=o1)
+    s0 = rrf.opts_steps_done(o1)
+    assert s0 == 3
+    o2 = rrf.make_opts(resume_steps=s0, track_frob=True, steps=steps)
+    A_nan = dev(np.full((m, n), np.nan))
+    U2, T2, V2 = rrf.randutv(A_nan, b, q, seed=5, opts=o2, out=(U, T, V))
+    assert rrf.opts_steps_done(o2) == steps
+    assert np.array_equal(host(U2), Uf) and np.array_equal(host(T2), Tf) and np.array_equal(host(V2), Vf)
+    fr = rrf.opts_frob(o2)
+    assert all(np.isnan(fr[:s0]))
+    assert abs(fr[s0] - eo[s0]) <= 1e-10 * eo[s0]
