@@ -292,7 +292,9 @@ def _factor(name: str, A, b: int, q: int, seed: int, opts=None, ws=None, out=Non
 
 
 def randutv(A, b: int, q: int, seed: int, opts=None, ws=None, out=None, stream=None, check_status=True):
-    """randUTV_basic (Algorithm 3) through rrf_randutv: returns (U, T, V) as column-major CUDA tensors."""
+    """rrf_randutv: randUTV_basic (Algorithm 3), or with opts randUTV_boosted (Algorithm 2), early termination
+    or resume (Sec. 4.1); m < n goes through A^T.  Returns (U, T, V) as column-major CUDA tensors; out=(U, A, V)
+    factors in place."""
     return _factor("rrf_randutv", A, b, q, seed, opts, ws, out, stream, check_status)
 
 
