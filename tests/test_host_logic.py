@@ -70,3 +70,21 @@ def test_boundary_ratios_use_the_spectral_norm():
     r = bench._boundary_ratios(torch, torch.from_numpy(T), s, 32, [32, 64])
     for k in (32, 64):
         assert abs(r[str(k)] - np.linalg.norm(T[k:, k:], 2) / s[k]) <= 1e-4 * r[str(k)]
+
+
+def test_input_recipes_have_the_prescribed_spectra():
+    """The seeded inputs are Q1 diag(s) Q2^T with the recipe's singular values (numpy's SVD recovers them),
+    and the 8192^2 spectrum is continuous at its plateau (s_{n/2 - 1} * 10^(-8/n) = 1e-4)."""
+    from paper_2106_13402_gb300 import testmats
+    for prof in ("exp100", "c2", "poly", "fast", "sshape", "step", "exp8"):
+        A, s = testmats.make_matrix(120, 96, prof, 5, 6)
+        assert abs(s[0] - 1.0) <= 1e-5 and np.all(np.diff(s) <= 0)   # the S-shape starts at 1 - 4e-6
+        sv = np.linalg.svd(A, compute_uv=False)
+        assert np.max(np.abs(sv - s)) <= 1e-13, prof
+    n = 8192
+    s = testmats.singular_values(n, "c2")
+    assert s[n // 2] == 1e-4 and abs(s[n // 2 - 1] * 10 ** (-8 / n) - 1e-4) <= 1e-18
+    A, s = testmats.make_matrix(60, 40, "rank", 1, 2, rank=8)
+    assert np.linalg.matrix_rank(A) == 8
+    G, none = testmats.make_matrix(30, 20, "gaussian", 3, 4)
+    assert none is None and G.flags["F_CONTIGUOUS"]
