@@ -29,6 +29,9 @@
  *  - `workspace` is caller-owned device memory of at least the size the matching *_workspace query
  *    returns, 256-byte aligned.  The library never allocates in the device entry points.  One
  *    workspace must not be used by two calls that overlap on the GPU.
+ *  - Host threads: calls may come from several threads at once, each with its own workspace.  Kernel
+ *    attributes (shared-memory sizes) are set once per process, on the device current at first use:
+ *    one process drives one GPU.
  *  - Errors: argument errors are detected on the host and returned immediately (nothing is
  *    enqueued); rrf_last_arg_error() then names the offending argument (1-based position, LAPACK
  *    style).  Device-side conditions (Jacobi sweep cap, barrier timeout, non-finite input) are

@@ -321,7 +321,7 @@ size_t tc_smem_bytes() {
 
 template <int BN>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p, int splits, cudaStream_t s) {
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // set once per process (one GPU each)
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_smem_bytes<BN>());

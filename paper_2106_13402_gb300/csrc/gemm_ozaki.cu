@@ -582,7 +582,7 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   count_launch();
   CUtensorMap ma, mb;
   if (!oz_map(&ma, As, M, Kp, BM) || !oz_map(&mb, Bs, N, Kp, BN)) return cudaErrorInvalidValue;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // set once per process (one GPU each)
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
     if (e != cudaSuccess) return e;

@@ -520,7 +520,7 @@ int jacobi_cluster_size() {
 
 template <int CL, bool PRE>
 cudaError_t launch_jacobi(const JacobiArgs& a, int c, cudaStream_t stream) {
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // set once per process (one GPU each)
   if (!attr) {
     cudaError_t e = set_jacobi_attrs<CL, PRE>();
     if (e != cudaSuccess) return e;
@@ -582,7 +582,7 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
     double* gs = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) +
                                            align_up((size_t)3 * c * c * sizeof(double), 256));
     const size_t gs_bytes = scratch_bytes - align_up((size_t)3 * c * c * sizeof(double), 256);
-    static bool attr_pre = false;
+    static std::atomic<bool> attr_pre{false};  // set once per process (one GPU each)
     if (!attr_pre) {
       e = cudaFuncSetAttribute(jacobi_f32_prepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(2 * kPreMaxC * kPreLd * sizeof(float)));

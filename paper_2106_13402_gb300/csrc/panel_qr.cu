@@ -343,7 +343,7 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   const size_t staged_bytes = dyn + (size_t)(a.rows_per | 1) * w * sizeof(double);
   a.staged = staged_bytes <= kSmemCap ? 1 : 0;
   if (a.staged) dyn = staged_bytes;
-  static bool attr_set = false;
+  static std::atomic<bool> attr_set{false};  // set once per process (one GPU each)
   if (!attr_set) {
     cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     attr_set = true;
