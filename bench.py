@@ -493,6 +493,7 @@ def run_c3_c5(args):
     ms = _timed(torch, lambda: rrf.randutv(A, b, q, 17, opts=fast, ws=ws, out=out, check_status=False), args.steps)
     rrf.gemm_profile_end()
     emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    bf_ms, bf_flops, bf_bytes, bf_launches = rrf.gemm_profile_bf16()
     launches = rrf.launch_count() - l0
     clocks = sampler.stop()
     st = rrf.lib().rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None))
@@ -551,6 +552,13 @@ def run_c3_c5(args):
                      "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                      "peak_source": f"{peak_src} bf16_tflops_sustained", "share_of_step": round(emu_ms / (ms * args.steps), 4),
                      "launches": int(emu_launches)},
+        # the BF16 sketch GEMM (tcgen05): HBM-bound skinny products, algorithmic bytes over its event time
+        "sketch_roofline": ({"kernel": "tc_gemm_kernel", "bound": "hbm",
+                             "achieved": round(bf_bytes / (bf_ms / 1e3) / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
+                             "unit": "GB/s", "frac": round(bf_bytes / (bf_ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]), 4),
+                             "traffic": None, "tflops": round(bf_flops / (bf_ms / 1e3) / 1e12, 2),
+                             "share_of_step": round(bf_ms / (ms * args.steps), 4), "launches": int(bf_launches)}
+                            if bf_ms > 0 else None),
         "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)

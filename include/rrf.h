@@ -329,11 +329,15 @@ RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
  * rrf_gemm_profile_emulated (after rrf_gemm_profile_end): the same for the tensor-core kernel of the
  *   emulated GEMM (its digit splitting and split-K reduction launches are not included): device time,
  *   FP64-equivalent flops 2 M N K, tensor flops 28 x 2 M N K' (K' = K rounded up to 32) and launches.
+ * rrf_gemm_profile_bf16 (after rrf_gemm_profile_end): the same for the tensor-core kernel of the BF16
+ *   sketch GEMM (its split-K reduction not included): device time, flops 2 M N K, algorithmic bytes
+ *   2 (M + N) K (BF16 operands read once) + 4 M N (one FP32 result per output) and launches.
  * ---------------------------------------------------------------------------------------------- */
 RRF_API int64_t rrf_launch_count(void);
 RRF_API int rrf_gemm_profile_begin(int max_launches);
 RRF_API int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches);
 RRF_API int rrf_gemm_profile_emulated(double* ms, double* flops, double* tensor_flops, int64_t* launches);
+RRF_API int rrf_gemm_profile_bf16(double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* Human-readable name of a status code (static storage). */
 RRF_API const char* rrf_status_string(rrf_status s);

@@ -372,9 +372,12 @@ cudaError_t gemm_bf16_tn(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A
   p.part = part;
   p.status = status;
   cudaError_t e;
+  // profiler: 2MNK BF16 flops; algorithmic bytes = the BF16 operands read once + one FP32 result each
+  cudaEvent_t ev_end = profile_launch_begin(2, 2.0 * M * N * K, 2.0 * (double)(M + N) * K + 4.0 * M * N, s);
   if (bn == 64) e = launch_tc<64>(ma, mb, p, splits, s);
   else if (bn == 128) e = launch_tc<128>(ma, mb, p, splits, s);
   else e = launch_tc<256>(ma, mb, p, splits, s);
+  if (ev_end != nullptr) cudaEventRecord(ev_end, s);
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((M * N + threads - 1) / threads, (int64_t)dev_info().sms * 16);

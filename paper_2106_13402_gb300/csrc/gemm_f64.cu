@@ -168,7 +168,8 @@ int plan_splits(const GemmDesc& d, int sms) {
 
 // Optional instrumentation: CUDA events around each launch (diagnostics API of rrf.h).
 // Event pairs around GEMM launches while profiling is on; kind 0 = DFMA GEMM (kernel + split-K reduce),
-// kind 1 = the emulated GEMM's tensor-core kernel.
+// kind 1 = the emulated GEMM's tensor-core kernel, kind 2 = the BF16 sketch GEMM's tensor-core kernel.
+constexpr int kKinds = 3;
 struct GemmProfile {
   std::mutex mu;
   bool on = false;
@@ -176,8 +177,8 @@ struct GemmProfile {
   std::vector<int> kind;
   std::vector<double> flops, tflops;
   size_t used = 0;
-  double ms_k[2] = {0.0, 0.0}, flops_k[2] = {0.0, 0.0}, tflops_k[2] = {0.0, 0.0};
-  int64_t launches_k[2] = {0, 0};
+  double ms_k[kKinds] = {}, flops_k[kKinds] = {}, tflops_k[kKinds] = {};
+  int64_t launches_k[kKinds] = {};
 };
 GemmProfile& prof() {
   static GemmProfile p;
@@ -286,7 +287,7 @@ extern "C" int rrf_gemm_profile_begin(int max_launches) {
   pf.flops.assign(pf.ev.size() / 2, 0.0);
   pf.tflops.assign(pf.ev.size() / 2, 0.0);
   pf.used = 0;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < rrf::kKinds; ++k) {
     pf.ms_k[k] = pf.flops_k[k] = pf.tflops_k[k] = 0.0;
     pf.launches_k[k] = 0;
   }
@@ -304,6 +305,7 @@ extern "C" int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches
       float t = 0.f;
       if (cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]) != cudaSuccess) return 1;
       const int k = pf.kind[i / 2];
+      if (k < 0 || k >= rrf::kKinds) continue;
       pf.ms_k[k] += t;
       pf.flops_k[k] += pf.flops[i / 2];
       pf.tflops_k[k] += pf.tflops[i / 2];
@@ -313,6 +315,17 @@ extern "C" int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches
   if (ms) *ms = pf.ms_k[0];
   if (flops) *flops = pf.flops_k[0];
   if (launches) *launches = pf.launches_k[0];
+  return 0;
+}
+
+extern "C" int rrf_gemm_profile_bf16(double* ms, double* flops, double* bytes, int64_t* launches) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  if (pf.on) return 1;
+  if (ms) *ms = pf.ms_k[2];
+  if (flops) *flops = pf.flops_k[2];
+  if (bytes) *bytes = pf.tflops_k[2];
+  if (launches) *launches = pf.launches_k[2];
   return 0;
 }
 

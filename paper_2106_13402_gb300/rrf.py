@@ -31,6 +31,7 @@ EXPORTED = [
     "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
     "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
     "rrf_gemm_emulated", "rrf_gemm_profile_emulated", "rrf_low_rank_workspace", "rrf_low_rank",
+    "rrf_gemm_profile_bf16",
 ]
 
 
@@ -148,6 +149,8 @@ def lib():
             L.rrf_gemm_profile_emulated.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [
                 ctypes.POINTER(ctypes.c_int64)]
             L.rrf_gemm_profile_emulated.restype = ctypes.c_int
+            L.rrf_gemm_profile_bf16.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.POINTER(ctypes.c_int64)]
+            L.rrf_gemm_profile_bf16.restype = ctypes.c_int
             L.rrf_low_rank_workspace.argtypes = [_i64, _i64, _i64]
             L.rrf_low_rank_workspace.restype = _sz
             L.rrf_low_rank.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]
@@ -470,6 +473,15 @@ def gemm_profile_emulated():
     if lib().rrf_gemm_profile_emulated(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(tf), ctypes.byref(n)) != 0:
         raise RuntimeError("rrf_gemm_profile_emulated failed")
     return ms.value, fl.value, tf.value, n.value
+
+
+def gemm_profile_bf16():
+    """After gemm_profile_end: (device ms, flops, algorithmic bytes, launches) of the BF16 sketch GEMM's
+    tensor-core kernel."""
+    ms, fl, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    if lib().rrf_gemm_profile_bf16(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by), ctypes.byref(n)) != 0:
+        raise RuntimeError("rrf_gemm_profile_bf16 failed")
+    return ms.value, fl.value, by.value, n.value
 
 
 def mlp_param_count() -> int:
