@@ -2,7 +2,7 @@
 
 Training data comes from the method itself: each training matrix A = Q1 diag(s) Q2^T (seeded Haar factors,
 a random decay class) is factored with q = 0 (recording the 16 features of every step through the C ABI)
-and with fixed q = 1, 2, 3; the judge is the rank-k error e_k = ||T(k:, k:)||_2 at every block boundary
+and with fixed q = 1, 2, 3; the criterion is the rank-k error e_k = ||T(k:, k:)||_2 at every block boundary
 k (Sec. 4.1).  A q is acceptable at a boundary when its e_k meets the quality target 1.1 sigma_{k+1}, or
 else comes within 5 % of the best of q = 2 (the fallback) and q = 3; the label is the cheapest acceptable
 q.  The MLP is trained on the GPU with the library's FP16 forward/backward kernels and Adam; at run time
