@@ -135,8 +135,9 @@ typedef struct rrf_opts {
  *
  * Early termination (Sec. 4.1; any sampling option).  With opts->frob_tol > 0 or opts->frob_out set, the
  * library evaluates e_0 = ||A||_F and, after each step i, e_i^2 = max(e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2, 0)
- * on the device (e_i = ||T(ib:, ib:)||_F up to rounding of order eps ||A||_F^2 / e_i; the last step gives
- * e = 0).  With frob_tol > 0 the call stops after the first step i >= 0 with e_i <= frob_tol (absolute):
+ * on the device (e_i = ||T(ib:, ib:)||_F up to rounding of order eps ||A||_F^2 / e_i; once e_i^2 falls
+ * below 2^-30 e_0^2, where that rounding would dominate, ||T(ib:, ib:)||_F is summed directly instead, so
+ * tolerances down to ~1e-13 ||A||_F stay meaningful; the last step gives e = 0).  With frob_tol > 0 the call stops after the first step i >= 0 with e_i <= frob_tol (absolute):
  * A = U T V^T still holds with U, V orthogonal, T's first ib columns are upper trapezoidal with diagonal
  * b x b blocks and T(ib:, ib:) is the unreduced trailing block (i = 0: T = A, U = I, V = I).  Checking the
  * tolerance synchronizes the stream once per step, so such a call cannot be captured in a CUDA graph.
@@ -264,7 +265,8 @@ RRF_API rrf_status rrf_panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, do
  * the workspace status word.  For 32 <= c <= 256 with rrf_jacobi_svd_workspace(c) bytes, FP32 sweeps
  * first give a starting V (made orthogonal in FP64 by two Newton-Schulz steps) and the FP64 sweeps run
  * on M V from there; the FP64 sweeps also stop after a sweep whose rotations all had
- * |gamma| <= 2^-30 sqrt(alpha beta).  A workspace of just the header size runs the FP64 sweeps from
+ * |gamma| <= 2^-30 sqrt(alpha beta) and tangent |t| <= 2^-24 (which keeps every normalized inner
+ * product of the result below about 2 c 2^-53, clusters included).  A workspace of just the header size runs the FP64 sweeps from
  * V = I. */
 RRF_API size_t rrf_jacobi_svd_workspace(int64_t c);
 RRF_API rrf_status rrf_jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,

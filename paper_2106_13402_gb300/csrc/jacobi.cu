@@ -11,7 +11,7 @@
 // are Hestenes': skip when |gamma| <= tol sqrt(alpha beta) (tol = c 2^-53), otherwise
 // zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1+t^2),
 // sn = cs t; stop after a sweep without rotations, or after one whose rotations all had
-// |gamma| <= 2^-30 sqrt(alpha beta) (cap 40 sweeps -> RRF_NOT_CONVERGED).
+// |gamma| <= 2^-30 sqrt(alpha beta) and |t| <= 2^-24 (cap 40 sweeps -> RRF_NOT_CONVERGED).
 // With scratch, an FP32 pre-pass (one CTA for c <= 128, the cluster kernel in FP32 above) gives the
 // starting V, two FP64 Newton-Schulz steps make it orthogonal, and the FP64 sweeps run on M V.
 // Outputs: sigma_k = ||m_k|| sorted descending (ties by index), u_k = m_k / sigma_k, and each pair
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
             gsn = gcs * tt;
             grot = 1;
             s_rot = 1;
-            if (fabs(G) > 0x1p-30 * sab) s_big = 1;
+            if (fabs(G) > 0x1p-30 * sab || fabs(tt) > 0x1p-24) s_big = 1;
           }
           }
         }
@@ -239,10 +239,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
       __syncthreads();
     }
     __syncthreads();
-    // Converged after a sweep without rotations, or after one whose every rotation had
-    // |gamma| <= 2^-30 sqrt(alpha beta): Jacobi converges quadratically, so the next sweep's
-    // off-diagonal terms would be ~2^-60 relative, below the tolerance c 2^-53, and rotate nothing
-    // that matters.  Every CTA holds the same totals, so all take the same decision.
+    // Converged after a sweep without rotations, or after one whose every rotation had both
+    // |gamma| <= 2^-30 sqrt(alpha beta) and |t| <= 2^-24.  A rotation of (p, q) by sin s moves the
+    // normalized inner product of p with any other column by about |s| |gamma_qr| sqrt(alpha_q / alpha_p),
+    // which these two bounds keep below 2^-53.5 (for alpha_q >= 2 alpha_p, s sqrt(alpha_q/alpha_p) is
+    // itself ~2 |gamma_pq| / sqrt(alpha_p alpha_q)); over the c - 1 rotations of a column that stays
+    // below the tolerance c 2^-53, so the next sweep would rotate nothing that matters.  The bound on t
+    // matters for clusters: a core close to a multiple of an orthogonal matrix has tiny gamma but
+    // alpha ~ beta, hence rotations up to pi/4 that mix columns and leave them non-orthogonal at the
+    // level of gamma itself.  Every CTA holds the same totals, so all take the same decision.
     converged = (s_rot == 0) || (!PRE && s_big == 0);
     __syncthreads();
     if (tid == 0) {

@@ -129,6 +129,27 @@ def test_jacobi_matches_oracle(c, kind):
         np.testing.assert_allclose(Vs, Vo, atol=1e-13 / gap)
 
 
+@pytest.mark.parametrize("c", [32, 64, 128, 200])
+@pytest.mark.parametrize("spread", [1e-6, 1e-9, 1e-12])
+def test_jacobi_clustered_core_is_orthogonal(c, spread):
+    # A core close to a multiple of an orthogonal matrix (a flat stretch of the spectrum): its columns
+    # are nearly orthogonal from the start, but alpha ~ beta makes every rotation large, so a stop on
+    # |gamma| alone leaves u_k = m_k / sigma_k non-orthogonal at the level of gamma (Hestenes' rule
+    # with tolerance c 2^-53 does not).
+    rng = np.random.default_rng(c + int(-np.log10(spread)))
+    Q1, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    s_true = 1e-2 * (1.0 + spread * np.arange(c))[::-1]
+    M = (Q1 * s_true) @ Q2.T
+    Us, s, Vs, st = rrf.jacobi_svd(dev(M))
+    Us, s, Vs = host(Us), host(s), host(Vs)
+    assert st == 0
+    np.testing.assert_allclose(s, s_true, rtol=1e-13)
+    np.testing.assert_allclose(Us @ np.diag(s) @ Vs.T, M, atol=1e-13 * np.abs(M).max())
+    assert np.abs(Us.T @ Us - np.eye(c)).max() <= 1e-13
+    assert np.abs(Vs.T @ Vs - np.eye(c)).max() <= 1e-13
+
+
 def test_jacobi_zero_and_diagonal_inputs():
     Us, s, Vs, st = rrf.jacobi_svd(dev(np.zeros((16, 16))))
     Us, s = host(Us), host(s)
