@@ -54,10 +54,17 @@ __global__ void finite_kernel(int64_t rows, int64_t cols, const double* __restri
 // grid-stride order, then one block sums the partials in a fixed tree, so the result is repeatable.
 constexpr int kSumsqThreads = 256;
 constexpr int kSumsqMaxBlocks = 1024;
+// The recurrence subtracts sums of squares of size up to e_0^2, so its absolute error is a few hundred
+// units of 2^-53 e_0^2 (rounding of the sums and of the subtraction, and the departure of the computed
+// transformations from orthogonality).  Once e_i^2 < 2^-30 e_0^2 that error would exceed ~2^-15 of the
+// value, so from there the norm of the trailing block is summed directly.
+constexpr double kFrobFloor = 0x1p-30;
 
+// gate == null: always run; else only when *gate != 0 (the partial sums are then zero)
 __global__ void sumsq_kernel(int64_t rows, int64_t cols, const double* __restrict__ X, int64_t ld,
-                             double* __restrict__ part) {
+                             double* __restrict__ part, const int* gate) {
   __shared__ double sh[kSumsqThreads];
+  if (gate != nullptr && *(volatile const int*)gate == 0) return;
   const int64_t total = rows * cols;
   double acc = 0.0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -74,9 +81,12 @@ __global__ void sumsq_kernel(int64_t rows, int64_t cols, const double* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// e2[idx] = the sum of the nblk partials (first), else max(e2[idx - 1] - that sum, 0).
-__global__ void frob_update_kernel(const double* __restrict__ part, int nblk, double* e2, int64_t idx, int first) {
+// mode 0: e2[idx] = the sum of the nblk partials.  mode 1: e2[idx] = max(e2[idx - 1] - sum, 0), and
+// *gate = (e2[idx] < kFrobFloor e2[base]).  mode 2: e2[idx] = sum when *gate != 0.
+__global__ void frob_update_kernel(const double* __restrict__ part, int nblk, double* e2, int64_t idx, int mode,
+                                   int64_t base, int* gate) {
   __shared__ double sh[kSumsqMaxBlocks];
+  if (mode == 2 && *(volatile const int*)gate == 0) return;
   double acc = 0.0;
   for (int t = threadIdx.x; t < nblk; t += blockDim.x) acc += part[t];
   sh[threadIdx.x] = acc;
@@ -85,7 +95,35 @@ __global__ void frob_update_kernel(const double* __restrict__ part, int nblk, do
     if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) e2[idx] = first ? sh[0] : fmax(e2[idx - 1] - sh[0], 0.0);
+  if (threadIdx.x == 0) {
+    if (mode == 1) {
+      const double v = fmax(e2[idx - 1] - sh[0], 0.0);
+      e2[idx] = v;
+      *gate = (v < kFrobFloor * e2[base]) ? 1 : 0;
+    } else {
+      e2[idx] = sh[0];
+    }
+  }
+}
+
+int64_t sumsq_grid(int64_t rows, int64_t cols) {
+  const int64_t total = std::max<int64_t>(rows, 0) * std::max<int64_t>(cols, 0);
+  return std::max<int64_t>(1, std::min<int64_t>((total + 4 * kSumsqThreads - 1) / (4 * kSumsqThreads),
+                                                kSumsqMaxBlocks));
+}
+
+cudaError_t frob_launch(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2,
+                        int64_t idx, int mode, int64_t base, int* gate, cudaStream_t s) {
+  const int64_t total = std::max<int64_t>(rows, 0) * std::max<int64_t>(cols, 0);
+  const int64_t grid = sumsq_grid(rows, cols);
+  sumsq_kernel<<<(unsigned)grid, kSumsqThreads, 0, s>>>(total > 0 ? rows : 1, total > 0 ? cols : 0, X, ld, part,
+                                                        mode == 2 ? gate : nullptr);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  frob_update_kernel<<<1, kSumsqMaxBlocks, 0, s>>>(part, (int)grid, e2, idx, mode, base, gate);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -93,17 +131,13 @@ __global__ void frob_update_kernel(const double* __restrict__ part, int nblk, do
 size_t frob_scratch_bytes() { return kSumsqMaxBlocks * sizeof(double); }
 
 cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2, int64_t idx,
-                      bool first, cudaStream_t s) {
-  const int64_t total = std::max<int64_t>(rows, 0) * std::max<int64_t>(cols, 0);
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 4 * kSumsqThreads - 1) / (4 * kSumsqThreads),
-                                                              kSumsqMaxBlocks));
-  sumsq_kernel<<<(unsigned)grid, kSumsqThreads, 0, s>>>(total > 0 ? rows : 1, total > 0 ? cols : 0, X, ld, part);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  frob_update_kernel<<<1, kSumsqMaxBlocks, 0, s>>>(part, (int)grid, e2, idx, first ? 1 : 0);
-  count_launch();
-  return cudaGetLastError();
+                      bool first, int64_t base, int* gate, cudaStream_t s) {
+  return frob_launch(rows, cols, X, ld, part, e2, idx, first ? 0 : 1, base, gate, s);
+}
+
+cudaError_t frob_refresh(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2,
+                         int64_t idx, int* gate, cudaStream_t s) {
+  return frob_launch(rows, cols, X, ld, part, e2, idx, 2, 0, gate, s);
 }
 
 cudaError_t fill_identity(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s) {

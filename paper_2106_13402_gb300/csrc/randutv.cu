@@ -405,10 +405,11 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   };
   bool stop = false;
   int64_t done = start;
+  int* fgate = &w.hdr->flags[8];  // set when the recurrence fell below its accuracy floor
   if (frob) {  // e_start from its definition: ||A||_F, or the trailing block's norm when resuming
     const int64_t o = b * start;
-    if (start == 0) RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, s));
-    else RRF_CUDA_TRY(frob_step(m - o, n - o, T + o + o * ldt, ldt, w.fpart, w.e2, start, true, s));
+    if (start == 0) RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, 0, fgate, s));
+    else RRF_CUDA_TRY(frob_step(m - o, n - o, T + o + o * ldt, ldt, w.fpart, w.e2, start, true, start, fgate, s));
     if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(start, &stop));
   }
   for (int64_t i = start + 1; i <= steps && !stop; ++i) {
@@ -513,8 +514,9 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         if (o > 0) RRF_CUDA_TRY(copy_matrix(o, b, w.Xc, o, TI1J2, ldt, s));
         RRF_CUDA_TRY(set_diag_block(r, b, w.sig, T22, ldt, s));
       }
-      if (frob) {  // e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2
-        RRF_CUDA_TRY(frob_step(b, c, T22, ldt, w.fpart, w.e2, i, false, s));
+      if (frob) {  // e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2; summed directly below the recurrence's floor
+        RRF_CUDA_TRY(frob_step(b, c, T22, ldt, w.fpart, w.e2, i, false, start, fgate, s));
+        RRF_CUDA_TRY(frob_refresh(r - b, c - b, T22 + b + b * ldt, ldt, w.fpart, w.e2, i, fgate, s));
         if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(i, &stop));
       }
     } else {

@@ -173,10 +173,14 @@ cudaError_t transpose_matrix(int64_t rows, int64_t cols, const double* S, int64_
 // zero the strictly lower triangle of an rows x cols block
 cudaError_t zero_lower(int64_t rows, int64_t cols, double* X, int64_t ld, cudaStream_t s);
 // Frobenius recurrence (Sec. 4.1): e2[idx] = ||X||_F^2 (first) or max(e2[idx - 1] - ||X||_F^2, 0); part holds
-// frob_scratch_bytes() of partial sums.
+// frob_scratch_bytes() of partial sums.  A recurrence step also sets *gate when e2[idx] fell below 2^-30
+// e2[base], where the recurrence is no longer accurate; frob_refresh then replaces e2[idx] by the directly
+// summed ||X||_F^2 of the trailing block X (and does nothing while *gate == 0).
 size_t frob_scratch_bytes();
 cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2, int64_t idx,
-                      bool first, cudaStream_t s);
+                      bool first, int64_t base, int* gate, cudaStream_t s);
+cudaError_t frob_refresh(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2,
+                         int64_t idx, int* gate, cudaStream_t s);
 // status |= NUMERICAL if any entry of the block is not finite
 cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status,
                          cudaStream_t s);

@@ -136,3 +136,39 @@ def test_stop_then_resume_equals_one_call(m, n, b, q, prof):
     fr = rrf.opts_frob(o2)
     assert all(np.isnan(fr[:s0]))
     assert abs(fr[s0] - eo[s0]) <= 1e-10 * eo[s0]
+
+
+def cliff_matrix(m, n, b, tail, seed):
+    rng = np.random.default_rng(seed)
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.where(np.arange(n) < b, 1.0, tail)
+    return np.asfortranarray((Q1 * s) @ Q2.T)
+
+
+def test_recurrence_floor_gives_true_trailing_norm():
+    """Below 2^-30 e_0^2 the recurrence is dominated by rounding (its absolute error is some units of
+    2^-53 ||A||_F^2 per step), so there the trailing block's norm is summed directly.  A cliff after the
+    first block (s_j = 1, then 1e-6) puts e_1^2 near 1e-11 e_0^2, where the recurrence would be off by
+    ~1e-5 relative; the reported e_1 .. e_{s-1} must match the oracle's trailing norms to 1e-7."""
+    m, n, b = 300, 250, 32
+    A = cliff_matrix(m, n, b, 1e-6, 77)
+    U, T, V, done, fr = run(A, b, 1, 3)
+    assert done == -(-n // b)
+    eo = oracle_e(A, b, 1, 3)
+    for k in range(1, len(eo) - 1):
+        assert abs(fr[k] - eo[k]) <= 1e-7 * eo[k], (k, fr[k], eo[k])
+
+
+def test_tolerance_near_rounding_level_stops_correctly():
+    """With s_j = 1e-9 after the first block, e_1 ~ 1.5e-8 is below the recurrence's own rounding error
+    (~1e-7 here).  A tolerance of 2 e_1 must stop after step 1, one of e_1 / 2 must not."""
+    m, n, b = 300, 250, 32
+    A = cliff_matrix(m, n, b, 1e-9, 78)
+    eo = oracle_e(A, b, 1, 3)
+    e1 = eo[1]
+    U, T, V, done, fr = run(A, b, 1, 3, frob_tol=2.0 * e1)
+    assert done == 1
+    assert abs(np.linalg.norm(T[b:, b:]) - fr[1]) <= 1e-4 * fr[1]
+    U, T, V, done, fr = run(A, b, 1, 3, frob_tol=0.5 * e1)
+    assert done >= 2
