@@ -63,6 +63,8 @@ def lib():
             L.orc_randutv.argtypes = [_i64, _i64, _dp, _i64, _i64, ctypes.c_int, ctypes.c_uint64, _dp, _i64,
                                       _dp, _i64, _dp, _i64, ctypes.c_int]
             L.orc_randutv.restype = ctypes.c_int
+            L.orc_randutv_reorth.argtypes = L.orc_randutv.argtypes
+            L.orc_randutv_reorth.restype = ctypes.c_int
             L.orc_randutv_boosted.argtypes = [_i64, _i64, _dp, _i64, _i64, ctypes.c_int, _i64, ctypes.c_uint64,
                                               _dp, _i64, _dp, _i64, _dp, _i64, ctypes.c_int]
             L.orc_randutv_boosted.restype = ctypes.c_int
@@ -167,6 +169,17 @@ def randutv(A, b: int, q: int, seed: int, max_steps: int = 0):
     T = np.zeros((m, n), order="F")
     V = np.zeros((n, n), order="F")
     st = lib().orc_randutv(m, n, _p(A), m, b, q, seed, _p(U), m, _p(T), m, _p(V), n, max_steps)
+    return U, T, V, int(st)
+
+
+def randutv_reorth(A, b: int, q: int, seed: int, max_steps: int = 0):
+    """randUTV_basic with the re-orthonormalized power iteration (Sec. 2.5 (ii)): returns (U, T, V, status)."""
+    A = _f64(A)
+    m, n = A.shape
+    U = np.zeros((m, m), order="F")
+    T = np.zeros((m, n), order="F")
+    V = np.zeros((n, n), order="F")
+    st = lib().orc_randutv_reorth(m, n, _p(A), m, b, q, seed, _p(U), m, _p(T), m, _p(V), n, max_steps)
     return U, T, V, int(st)
 
 

@@ -400,8 +400,13 @@ static void left_mul_small_t(int64_t k, int64_t cols, double* C, int64_t ldc, co
   free(tmp);
 }
 
-int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
-                double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps) {
+static void thin_q(int64_t rows, int64_t k, const double* X, int64_t ldx, double* Q, int64_t ldq);
+
+/* randUTV_basic; reorth != 0 orthonormalizes the sample before every application of T22 and of T22^T
+ * (the power iteration with re-orthonormalization of Sec. 2.5 (ii), recommended again in Sec. 4.3). */
+static int randutv_impl(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
+                        double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps,
+                        int reorth) {
   if (m < n || n < 1 || b < 1 || q < 0 || lda < m || ldu < m || ldt < m || ldv < n) return 1;
   int status = 0;
   /* T = A; U = I_m; V = I_n. */
@@ -423,6 +428,7 @@ int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, i
   double* Usm = (double*)malloc(sizeof(double) * (size_t)b * (size_t)b);
   double* Vsm = (double*)malloc(sizeof(double) * (size_t)b * (size_t)b);
   double* sig = (double*)malloc(sizeof(double) * (size_t)b);
+  double* Qo = reorth ? (double*)malloc(sizeof(double) * (size_t)m * (size_t)b) : NULL;
 
   for (int64_t i = 1; i <= s; ++i) {
     if (max_steps > 0 && i > max_steps) break;
@@ -430,11 +436,20 @@ int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, i
     const int64_t r = m - o, c = n - o;
     double* T22 = T + IDX(o, o, ldt);
     if (b * i < m && b * i < n) {
-      /* G = randn(m - b(i-1), b); Y = T22^T G; Y = T22^T (T22 Y) q times. */
+      /* G = randn(m - b(i-1), b); Y = T22^T G; Y = T22^T (T22 Y) q times.  With reorth the input of
+       * each application is replaced by an orthonormal basis of its columns (thin Q of its HQR). */
       orc_randn(r, b, G, r, seed, (uint32_t)i, 1u);
       orc_gemm('T', 'N', c, b, r, 1.0, T22, ldt, G, r, 0.0, Y, c);
       for (int j = 0; j < q; ++j) {
+        if (reorth) {
+          thin_q(c, b, Y, c, Qo, c);
+          copy_block(c, b, Qo, c, Y, c);
+        }
         orc_gemm('N', 'N', r, b, c, 1.0, T22, ldt, Y, c, 0.0, Z, r);
+        if (reorth) {
+          thin_q(r, b, Z, r, Qo, r);
+          copy_block(r, b, Qo, r, Z, r);
+        }
         orc_gemm('T', 'N', c, b, r, 1.0, T22, ldt, Z, r, 0.0, Y, c);
       }
       /* [V_i, ~] = HQR_full(Y); T(:, J2 u J3) <- T(:, J2 u J3) V_i; V(:, J2 u J3) <- V(:, J2 u J3) V_i. */
@@ -496,8 +511,18 @@ int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, i
     }
   }
   free(G); free(Y); free(Z); free(P); free(tauv); free(tauu);
-  free(Rs); free(Usm); free(Vsm); free(sig);
+  free(Rs); free(Usm); free(Vsm); free(sig); free(Qo);
   return status;
+}
+
+int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
+                double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps) {
+  return randutv_impl(m, n, A, lda, b, q, seed, U, ldu, T, ldt, V, ldv, max_steps, 0);
+}
+
+int orc_randutv_reorth(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
+                       double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps) {
+  return randutv_impl(m, n, A, lda, b, q, seed, U, ldu, T, ldt, V, ldv, max_steps, 1);
 }
 
 /* ---------------------------------------------------------------------------------------------

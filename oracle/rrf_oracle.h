@@ -63,6 +63,14 @@ int orc_jacobi_svd(int64_t r, int64_t c, const double* M, int64_t ldm, double* U
 int orc_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
                 double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps);
 
+/* randUTV_basic with the power iteration re-orthonormalized (Sec. 2.5 (ii); Sec. 4.3): in step i,
+ * Y = T22^T G, then q times { Y <- thin Q of HQR(Y); Z = T22 Y; Z <- thin Q of HQR(Z); Y = T22^T Z }.
+ * Everything else, and the Gaussian stream, as orc_randutv.  In exact arithmetic step 1 samples the
+ * same subspace as orc_randutv; in floating point it keeps directions that the plain iteration loses
+ * below about eps^(1/(2q+1)) of the block's largest singular value. */
+int orc_randutv_reorth(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, uint64_t seed,
+                       double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, int max_steps);
+
 /* randUTV_boosted (Algorithm 2) with oversampling p and recycled samples; p = 0 samples the subspace of
  * randUTV_basic (q >= 1).  Same outputs and conventions as orc_randutv. */
 int orc_randutv_boosted(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, int64_t p,

@@ -518,3 +518,88 @@ def test_boosted_reaches_boundary_target_where_basic_does_not():
     assert max(rb) > 1.1
     assert max(ro) <= 1.1
     assert np.mean(ro) < np.mean(rb)
+
+
+# ------------------------------------------------------------------ re-orthonormalized power iteration --
+def test_reorth_q0_is_randutv_basic():
+    """With q = 0 there is nothing to re-orthonormalize: the same factorization bit for bit."""
+    A, _ = testmats.make_matrix(120, 100, "exp8", 1, 2)
+    r0 = oracle.randutv(A, 16, 0, 5)
+    r1 = oracle.randutv_reorth(A, 16, 0, 5)
+    for x, y in zip(r0[:3], r1[:3]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_reorth_step1_equals_randomized_range(q):
+    """In exact arithmetic the orthonormalizations only change the basis of the sample, not its span, so
+    step 1 still gives U(:, :b) spanning (A A^T)^(q+1) G (Sec. 2.5 (ii) against Sec. 4.1): the numpy route
+    of the plain test, and the plain oracle's first block, both agree with it."""
+    A, s = testmats.make_matrix(60, 50, "exp100", 1, 2)
+    A = A * np.exp(-np.arange(50) / 8.0)
+    b, seed = 8, 21
+    U, T, V, st = oracle.randutv_reorth(A, b, q, seed)
+    assert st == 0
+    check_utv(A, U, T, V, b)
+    G = oracle.randn(60, b, seed, 1, 1)
+    W = G.copy()
+    for _ in range(q + 1):
+        W = A @ (A.T @ W)
+    Q, _ = np.linalg.qr(W)
+    e_route = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+    assert abs(ek_spectral(T, b) - e_route) <= 1e-10 * e_route
+    np.testing.assert_allclose(U[:, :b] @ U[:, :b].T, Q @ Q.T, atol=1e-9)
+    Up, Tp, Vp, _ = oracle.randutv(A, b, q, seed, max_steps=1)
+    np.testing.assert_allclose(np.diag(T)[:b], np.diag(Tp)[:b], rtol=1e-10)
+    np.testing.assert_allclose(V[:, :b] @ V[:, :b].T, Vp[:, :b] @ Vp[:, :b].T, atol=1e-9)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4])
+def test_reorth_keeps_what_the_plain_iteration_loses(q):
+    """Sec. 2.5: without re-orthonormalization the power iteration loses the directions below about
+    eps^(1/(2q+1)) sigma_max.  With sigma_j = 10^(-j/2) the b = 8 directions of the first block span
+    10^3.5, so the plain sketch (singular values raised to 2q+1 >= 5) drowns the last of them in
+    rounding and e_b stays near sigma_b; re-orthonormalized, e_b meets sigma_{b+1} (Eckart-Young
+    optimum) to 1 %."""
+    n, b = 96, 8
+    rng = np.random.default_rng(0)
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sv = 10.0 ** (-np.arange(n) / 2.0)
+    A = np.asfortranarray((Q1 * sv) @ Q2.T)
+    _, Tp, _, _ = oracle.randutv(A, b, q, 7, max_steps=1)
+    U, Tr, V, st = oracle.randutv_reorth(A, b, q, 7, max_steps=1)
+    assert st == 0
+    assert np.linalg.norm(A - U @ Tr @ V.T) <= 1e-12 * np.linalg.norm(A)
+    ep = ek_spectral(Tp, b) / sv[b]
+    er = ek_spectral(Tr, b) / sv[b]
+    assert er <= 1.01, er
+    assert ep >= 2.0, ep
+
+
+def test_reorth_factorization_is_exact_on_ragged_sizes():
+    A, s = testmats.make_matrix(130, 101, "fast", 3, 4)
+    U, T, V, st = oracle.randutv_reorth(A, 24, 2, 13)
+    assert st == 0
+    check_utv(A, U, T, V, 24)
+    assert all(ek_spectral(T, k) >= s[k] * (1 - 1e-10) for k in range(24, 101, 24))
+
+
+def test_reorth_every_application_sees_orthonormal_input():
+    """A first block spanning 10^8.4 (sigma_j = 10^(-1.2 j), j < b) followed by a flat tail at sigma_b / 2:
+    if the sample entering an application of T22 were not orthonormal, its smallest direction would meet
+    a dynamic range of 10^16.8 > 1/eps and be lost, and with the flat tail nothing brings it back.
+    Orthonormalized before every application (Sec. 2.5 (ii)), q = 2 gets e_b within 1 % of sigma_{b+1};
+    the plain iteration is off by more than 5x."""
+    n, b = 96, 8
+    rng = np.random.default_rng(0)
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    j = np.arange(n)
+    sv = np.where(j < b, 10.0 ** (-1.2 * j), 10.0 ** (-1.2 * (b - 1)) * 0.5 * np.exp(-(j - b) / 200.0))
+    A = np.asfortranarray((Q1 * sv) @ Q2.T)
+    _, Tp, _, _ = oracle.randutv(A, b, 2, 7, max_steps=1)
+    _, Tr, _, st = oracle.randutv_reorth(A, b, 2, 7, max_steps=1)
+    assert st == 0
+    assert ek_spectral(Tr, b) / sv[b] <= 1.01
+    assert ek_spectral(Tp, b) / sv[b] >= 5.0
