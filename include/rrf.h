@@ -293,8 +293,10 @@ RRF_API rrf_status rrf_low_rank(int64_t m, int64_t n, int64_t k, const double* U
  * until the process exits; w <= 256 with up to 152 cooperating CTAs fits (larger needs return
  * RRF_UNSUPPORTED).  All calls share the array, so calls that overlap on the GPU (different
  * streams, or threads) race and must be serialized by the caller.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating library routine. */
+ * looks up the array's device address (cudaGetSymbolAddress) and sets the panel kernel's shared-memory
+ * attribute on that device; make that first call before any stream capture.  Unlike the other entry
+ * points (one GPU per process), this one may be called on any device of the process, with that device
+ * current.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating library routine. */
 RRF_API rrf_status rrf_panel_qr_noalloc(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, double* Y,
                                         int64_t ldy, int* status, void* stream);
 
@@ -340,6 +342,25 @@ RRF_API int rrf_gemm_profile_begin(int max_launches);
 RRF_API int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches);
 RRF_API int rrf_gemm_profile_emulated(double* ms, double* flops, double* tensor_flops, int64_t* launches);
 RRF_API int rrf_gemm_profile_bf16(double* ms, double* flops, double* bytes, int64_t* launches);
+
+/* ------------------------------------------------------------------------------------------------
+ * Failure injection for tests (not part of the method; no counterpart in the paper).  Drives the
+ * bounded-wait and sweep-cap paths on purpose, without faulting or hanging the GPU:
+ *   RRF_INJECT_NONE          -- normal operation (default).
+ *   RRF_INJECT_PANEL_STALL   -- the Householder panel kernel's grid barrier waits for one CTA more
+ *                               than it launched, so no barrier completes; every CTA gives up after
+ *                               `value` clock cycles (>= 1), records RRF_TIMEOUT and returns.
+ *   RRF_INJECT_GEMM_STALL    -- in the emulated FP64 GEMM's tensor-core kernel the MMA warp first
+ *                               waits `value` cycles on a barrier nothing arrives on, then aborts: no
+ *                               MMA is issued, the other warps give up after their normal limit (~2 s),
+ *                               the tile copies already in flight are waited for, TMEM is released, and
+ *                               RRF_TIMEOUT is recorded.
+ *   RRF_INJECT_JACOBI_CAP    -- the FP64 Jacobi sweeps are capped at `value` (>= 1) instead of 40, so a
+ *                               matrix that needs more sweeps records RRF_NOT_CONVERGED.
+ * The setting is process-wide and applies to every call made while it is active; results of those
+ * calls are not meaningful.  Returns RRF_INVALID_ARG for an unknown kind or value < 1. */
+enum { RRF_INJECT_NONE = 0, RRF_INJECT_PANEL_STALL = 1, RRF_INJECT_GEMM_STALL = 2, RRF_INJECT_JACOBI_CAP = 3 };
+RRF_API rrf_status rrf_test_inject(int kind, long long value);
 
 /* Human-readable name of a status code (static storage). */
 RRF_API const char* rrf_status_string(rrf_status s);

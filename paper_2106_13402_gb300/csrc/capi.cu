@@ -11,6 +11,14 @@ namespace rrf {
 namespace {
 thread_local int g_arg_error = 0;
 std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_inject_kind{0};
+std::atomic<long long> g_inject_value{0};
+}
+Inject inject_state() {
+  Inject x;
+  x.kind = g_inject_kind.load(std::memory_order_relaxed);
+  x.value = g_inject_value.load(std::memory_order_relaxed);
+  return x;
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -55,6 +63,15 @@ extern "C" const char* rrf_status_string(rrf_status s) {
 }
 
 extern "C" int rrf_last_arg_error(void) { return g_arg_error; }
+
+extern "C" rrf_status rrf_test_inject(int kind, long long value) {
+  clear_arg_error();
+  if (kind < RRF_INJECT_NONE || kind > RRF_INJECT_JACOBI_CAP) { set_arg_error(1); return RRF_INVALID_ARG; }
+  if (kind != RRF_INJECT_NONE && value < 1) { set_arg_error(2); return RRF_INVALID_ARG; }
+  g_inject_value.store(kind == RRF_INJECT_NONE ? 0 : value);
+  g_inject_kind.store(kind);
+  return RRF_OK;
+}
 
 extern "C" int64_t rrf_launch_count(void) { return g_launches.load(); }
 

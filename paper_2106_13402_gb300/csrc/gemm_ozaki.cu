@@ -62,6 +62,8 @@ struct OzParams {
   int64_t ldc;
   int ct;               // write C^T: element (row, col) at C[col + row ldc]
   int* status;
+  long long stall_cycles;  // failure injection only (0 normally): the MMA warp first waits this long on a
+                           // barrier nothing arrives on, then aborts
 };
 
 // Work unit u -> (row tile, column tile, split).  Splits outermost; inside a split, groups of kGroupM row
@@ -107,12 +109,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitCycles); }
 // All 7 digit slices of a tile in one load: box (32 of K, rows, 7 slices), slices stacked in shared memory.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
   asm volatile(
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t empty_bar[kStages];
   __shared__ __align__(8) uint64_t acc_full[2];
   __shared__ __align__(8) uint64_t acc_empty[2];
+  __shared__ __align__(8) uint64_t never_bar;  // failure injection: nothing ever arrives on it
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], kEpiWarps);
     }
+    mbar_init(&never_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -225,6 +230,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
       int64_t g = 0;
       bool run = true;
+      if (p.stall_cycles > 0 && !mbar_wait_for(&never_bar, 0, p.stall_cycles)) {
+        set_status(p.status, RRF_TIMEOUT);
+        atomicExch(&abort_flag, 1);
+        run = false;
+      }
       for (int64_t u = blockIdx.x; u < p.units && run; u += gridDim.x) {
         int64_t m0, n0, k0;
         int split;
@@ -601,6 +611,8 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   p.ldc = d.ldc;
   p.ct = out_transposed ? 1 : 0;
   p.status = status;
+  const Inject inj = inject_state();
+  p.stall_cycles = inj.kind == RRF_INJECT_GEMM_STALL ? inj.value : 0;
   const unsigned grid = (unsigned)std::min<int64_t>(p.units, sms);
   // profiled work: the FP64 product's 2 M N K, and the tensor work 28 x 2 M N Kp of the digit products
   cudaEvent_t ev_end = profile_launch_begin(1, 2.0 * M * N * K, 56.0 * M * N * Kp, s);

@@ -53,6 +53,7 @@ struct JacobiArgs {
   const double* V0;  // optional starting V (c x c, orthogonal); null = identity
   int64_t ldv0;
   WsHeader* hdr;
+  int max_sweeps;    // FP64 sweeps before RRF_NOT_CONVERGED (kMaxSweeps; lower only under failure injection)
 };
 
 __device__ __forceinline__ void round_pair(int t, int k, int ne, int& p, int& q) {
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ Jaco
   int par = 0;
   int sweep = 0;
   bool converged = false;
-  const int max_sweeps = PRE ? kPreSweeps : kMaxSweeps;
+  const int max_sweeps = PRE ? kPreSweeps : a.max_sweeps;
   for (sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
     for (int t = 0; t < rounds; ++t) {
       int p = 0, q = 0;
@@ -575,6 +576,8 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   a.V0 = nullptr;
   a.ldv0 = 0;
   a.hdr = hdr;
+  const Inject inj = inject_state();
+  a.max_sweeps = inj.kind == RRF_INJECT_JACOBI_CAP ? (int)std::min<long long>(inj.value, kMaxSweeps) : kMaxSweeps;
   cudaError_t e;
   const size_t need = jacobi_scratch_bytes(c);
   if (scratch != nullptr && need > 0 && scratch_bytes >= need) {

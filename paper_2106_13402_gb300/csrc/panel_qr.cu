@@ -41,10 +41,13 @@ struct PanelArgs {
   int nb;
   int64_t rows_per;
   int staged;        // 1: this CTA's rows live in shared memory for the whole kernel
+  unsigned bar_extra;  // participants the barrier waits for beyond the grid (0; 1 under failure injection)
+  long long wait_cycles;  // how long a barrier wait lasts before it gives up
 };
 
-// Bounded grid barrier.  Returns false (and records RRF_TIMEOUT) if the wait gave up.
-__device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, unsigned& gen, int* s_fail) {
+// Bounded grid barrier over nblocks participants, each wait limited to wait_cycles.  Returns false (and
+// records RRF_TIMEOUT) if the wait gave up.
+__device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, long long wait_cycles, unsigned& gen, int* s_fail) {
   __syncthreads();
   if (threadIdx.x == 0) {
     *s_fail = 0;
@@ -59,7 +62,7 @@ __device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, unsigned& gen, int* s
       const long long t0 = clock64();
       volatile unsigned* g = &hdr->bar_gen;
       while (*g != target) {
-        if (clock64() - t0 > kBarrierCycles) {
+        if (clock64() - t0 > wait_cycles) {
           set_status(&hdr->status, RRF_TIMEOUT);
           *s_fail = 1;
           break;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
   column_partials(a, 0, Pl, ldl, i0, nloc, xs, a.partials + cta);
   if (i0 == 0 && nloc > 0)
     for (int k = tid; k < w; k += NT) a.rowbuf[k] = Pl[(int64_t)k * ldl];
-  if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
+  if (!grid_sync(a.hdr, gridDim.x + a.bar_extra, a.wait_cycles, gen, &s_fail)) return;
 
   for (int j = 0; j < w; ++j) {
     const int par = j & 1;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
         const int64_t lj = (j + 1) - i0;
         for (int k = j + 1 + tid; k < w; k += NT) rb[k] = Pl[lj + (int64_t)k * ldl];
       }
-      if (!grid_sync(a.hdr, gridDim.x, gen, &s_fail)) return;
+      if (!grid_sync(a.hdr, gridDim.x + a.bar_extra, a.wait_cycles, gen, &s_fail)) return;
     }
   }
   // Write back (staged), explicit reflectors Y (unit diagonal, zeros above), optional clean copy of R.
@@ -338,15 +341,25 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   a.hdr = hdr;
   a.nb = nb;
   a.rows_per = (r + nb - 1) / nb;
+  const Inject inj = inject_state();
+  const bool stall = inj.kind == RRF_INJECT_PANEL_STALL;
+  a.bar_extra = stall ? 1u : 0u;
+  a.wait_cycles = stall ? inj.value : kBarrierCycles;
   constexpr size_t kSmemCap = 200 * 1024;
   size_t dyn = (size_t)2 * a.rows_per * sizeof(double);
   const size_t staged_bytes = dyn + (size_t)(a.rows_per | 1) * w * sizeof(double);
   a.staged = staged_bytes <= kSmemCap ? 1 : 0;
   if (a.staged) dyn = staged_bytes;
-  static std::atomic<bool> attr_set{false};  // set once per process (one GPU each)
-  if (!attr_set) {
-    cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    attr_set = true;
+  // Function attributes belong to the device that is current when they are set: once per device (ids
+  // 0..63; the entry point without a workspace may be called on any device of the process).
+  static std::atomic<unsigned long long> attr_set{0};
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur < 0 || cur >= 64) cur = 0;
+  const unsigned long long bit = 1ull << cur;
+  if (!(attr_set.load() & bit)) {
+    e = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    if (e != cudaSuccess) return e;
+    attr_set.fetch_or(bit);
   }
   if (dyn > kSmemCap) return cudaErrorInvalidValue;
   void* args[] = {(void*)&a};

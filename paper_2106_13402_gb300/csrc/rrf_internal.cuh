@@ -66,6 +66,13 @@ void count_launch();
 // adjust the counter by n (negative for captured-but-not-launched kernels, positive per graph replay)
 void add_launches(int64_t n);
 
+// ---- failure injection for tests (rrf_test_inject): kind RRF_INJECT_*, and its value ------------------
+struct Inject {
+  int kind = 0;
+  long long value = 0;
+};
+Inject inject_state();
+
 // ---- thread-local argument-error slot ------------------------------------------------------------
 void set_arg_error(int pos);
 void clear_arg_error();

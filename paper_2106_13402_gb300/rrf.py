@@ -31,7 +31,7 @@ EXPORTED = [
     "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
     "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
     "rrf_gemm_emulated", "rrf_gemm_profile_emulated", "rrf_low_rank_workspace", "rrf_low_rank",
-    "rrf_gemm_profile_bf16",
+    "rrf_gemm_profile_bf16", "rrf_test_inject",
 ]
 
 
@@ -55,6 +55,7 @@ class Opts(ctypes.Structure):
 
 Q_FIXED, Q_LEARNED = 0, 1
 GEMM_AUTO, GEMM_NATIVE, GEMM_EMULATED = 0, 1, 2
+INJECT_NONE, INJECT_PANEL_STALL, INJECT_GEMM_STALL, INJECT_JACOBI_CAP = 0, 1, 2, 3
 
 
 _i64 = ctypes.c_int64
@@ -155,6 +156,8 @@ def lib():
             L.rrf_low_rank_workspace.restype = _sz
             L.rrf_low_rank.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]
             L.rrf_low_rank.restype = ctypes.c_int
+            L.rrf_test_inject.argtypes = [ctypes.c_int, ctypes.c_longlong]
+            L.rrf_test_inject.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -482,6 +485,27 @@ def gemm_profile_bf16():
     if lib().rrf_gemm_profile_bf16(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by), ctypes.byref(n)) != 0:
         raise RuntimeError("rrf_gemm_profile_bf16 failed")
     return ms.value, fl.value, by.value, n.value
+
+
+def test_inject(kind: int, value: int = 1):
+    """rrf_test_inject: drive a bounded wait or the Jacobi sweep cap into its failure path (tests only);
+    INJECT_NONE restores normal operation."""
+    _check(lib().rrf_test_inject(int(kind), int(value)), "rrf_test_inject")
+
+
+class injected:
+    """Context manager: failure injection `kind` with `value` inside the block, normal operation after."""
+
+    def __init__(self, kind: int, value: int):
+        self.kind, self.value = kind, value
+
+    def __enter__(self):
+        test_inject(self.kind, self.value)
+        return self
+
+    def __exit__(self, *exc):
+        test_inject(INJECT_NONE, 0)
+        return False
 
 
 def mlp_param_count() -> int:

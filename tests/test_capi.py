@@ -231,3 +231,13 @@ def test_batch_shapes_are_seeded_and_in_range():
     assert s1 == testmats.batch_shapes(512, 31)
     assert all(256 <= m <= 2048 and 128 <= n <= m for m, n in s1)
     assert len(set(s1)) > 400
+
+
+def test_failure_injection_arguments(L):
+    """rrf_test_inject validates its arguments on the host and can always be switched off."""
+    assert L.rrf_test_inject(9, 1) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 1
+    assert L.rrf_test_inject(rrf.INJECT_PANEL_STALL, 0) == rrf.RRF_INVALID_ARG
+    assert L.rrf_last_arg_error() == 2
+    assert L.rrf_test_inject(rrf.INJECT_JACOBI_CAP, -3) == rrf.RRF_INVALID_ARG
+    assert L.rrf_test_inject(rrf.INJECT_NONE, 0) == rrf.RRF_OK

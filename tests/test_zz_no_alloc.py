@@ -45,7 +45,8 @@ def _noalloc(L, P):
     return P, tau, Y, int(status.item())
 
 
-@pytest.mark.parametrize("shapes", [((3000, 128), (777, 64)), ((4100, 256), (4100, 256))])
+@pytest.mark.parametrize("shapes", [((3000, 128), (777, 64)), ((4100, 256), (4100, 256)),
+                                    ((152 * 64 + 37, 256), (20000, 256))])
 def test_noalloc_panel_matches_workspace_panel_twice(L, shapes):
     for call, (r, w) in enumerate(shapes):
         rng = np.random.default_rng(100 * call + r + w)
@@ -64,6 +65,9 @@ def test_noalloc_panel_matches_workspace_panel_twice(L, shapes):
 
 
 def test_noalloc_rejects_out_of_range_sizes(L):
+    """Arguments are checked on the host.  The size check against the 2 MiB array (RRF_UNSUPPORTED) is not
+    reachable on this GPU: with one CTA per SM (152) and w <= 256 the panel needs at most 1,151,232 bytes,
+    which the largest case above (r >= 152 x 64, w = 256, all 152 CTAs) exercises."""
     fake = ctypes.c_void_p(0x10000)
     assert L.rrf_panel_qr_noalloc(1000, 257, fake, 1000, fake, fake, 1000, None, None) == rrf.RRF_INVALID_ARG
     assert L.rrf_last_arg_error() == 2
