@@ -27,10 +27,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "factorizations/s (randUTV + powerURV, FP64, 8192^2, b=128, q=1)"
 WORKLOAD = "randUTV_basic + powerURV on 8192x8192 A = Q1 diag(s) Q2^T, s_j = 10^(-8j/n) (j < n/2) then 1e-4"
-# DRAM bytes (read + write) of one ozaki_gemm_kernel launch of the --workload gemm case, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on this command with the kernel as it is now; set it to
-# None whenever that kernel changes.
-GEMM_4096_DRAM_BYTES = 2.4968e9 + 0.1329e9
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ozaki_gemm_kernel taken from ncu captures
+# summarised under profiles/ (figures copied from those files, not measured by this script).  Each entry
+# names the source of the kernel it was taken on (sha1 of csrc/gemm_ozaki.cu); when that file has changed
+# since, the figure no longer describes the kernel and the line reports traffic as null.
+OZAKI_TRAFFIC = {
+    "gemm_4096": {"bytes_per_launch": None, "kernel_sha1": None, "profile": None},
+    "step_8192": {"bytes_per_launch": None, "kernel_sha1": None, "profile": None},
+}
 # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (measured 1.19 TFLOP/s at 1995 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -47,7 +51,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true")
-    p.add_argument("--cpu-sample-steps", type=int, default=2, help="randUTV steps the oracle runs per sample")
+    p.add_argument("--cpu-pow-n", type=int, default=2048, help="size of the matrix powerURV is timed on (oracle)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the learned-q + BF16-sketch and randUTV_boosted sub-results of the default line")
+    p.add_argument("--plain-reps", type=int, default=3, help="runs of the plain FP64 comparison per method")
     p.add_argument("--methods", default="randutv,powerurv", help="comma list (profiling runs may time one)")
     p.add_argument("--gemm", default="auto", choices=["auto", "native", "emulated"],
                    help="FP64 products: library default, DFMA only, or emulated on the BF16 tensor cores")
@@ -60,6 +67,23 @@ def parse():
                         "boosted: randUTV_boosted 8192^2, b=128, q=2, p=--oversample")
     p.add_argument("--oversample", type=int, default=128, help="p of the boosted workload")
     return p.parse_args()
+
+
+def ozaki_sha1() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2106_13402_gb300", "csrc", "gemm_ozaki.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def ozaki_traffic(which: str):
+    """(bytes per launch, source) of the recorded ncu capture, or (None, why) when there is none for the
+    kernel as it is now."""
+    t = OZAKI_TRAFFIC[which]
+    if t["bytes_per_launch"] is None:
+        return None, "no capture recorded"
+    if t["kernel_sha1"] != ozaki_sha1():
+        return None, f"kernel changed since {t['profile']}"
+    return t["bytes_per_launch"], f"ncu capture, {t['profile']} (copied, not measured here)"
 
 
 def measured_peaks():
@@ -156,24 +180,51 @@ def step_flops(n, b, q):
     return testmats.flops_randutv(n, n, b, q) + testmats.flops_powerurv(n, n, q)
 
 
-def cpu_sample(A_np, n, b, q, sample_steps):
-    """Time the oracle (as it stands) on the first `sample_steps` randUTV steps of the same matrix and
-    extrapolate its flop rate to one full step (randUTV + powerURV) by the flop model."""
+def cpu_rates(A_np, n, b, q, pow_n, pow_rate=None):
+    """The oracle as it stands on the host cores, on a bounded sample of the step: randUTV's first step
+    of the same n x n matrix (its public entry point with max_steps = 1), and, unless its rate is given,
+    powerURV in full on a pow_n x pow_n matrix of the same recipe.  Returns the measured seconds and each
+    method's rate (flop model / seconds)."""
     import oracle
     from paper_2106_13402_gb300 import testmats
 
-    sample_flops = testmats.flops_randutv(n, n, b, q, max_steps=sample_steps)
+    f_rand = testmats.flops_randutv(n, n, b, q, max_steps=1)
     t0 = time.perf_counter()
-    oracle.randutv(A_np, b, q, seed=17, max_steps=sample_steps)
-    dt = time.perf_counter() - t0
-    rate = sample_flops / dt
-    per_step_s = step_flops(n, b, q) / rate
-    return {"value": 2.0 / per_step_s, "unit": "factorizations/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": (f"first {sample_steps} of {n // b} randUTV steps of the same {n}x{n} matrix "
-                       f"({sample_flops / 1e9:.0f} GFLOP in {dt:.1f} s, {rate / 1e9:.2f} GFLOP/s), "
-                       f"extrapolated to one randUTV + powerURV step by the flop model"),
-            "seconds": dt}
+    oracle.randutv(A_np, b, q, seed=17, max_steps=1)
+    t_rand = time.perf_counter() - t0
+    out = {"randutv_s": t_rand, "randutv_rate": f_rand / t_rand, "randutv_gflop": f_rand / 1e9}
+    if pow_rate is None:
+        Ap, _ = testmats.make_matrix(pow_n, pow_n, "c2", 11, 12, device="cpu")
+        f_pow = testmats.flops_powerurv(pow_n, pow_n, q)
+        t0 = time.perf_counter()
+        oracle.powerurv(Ap, q, seed=17)
+        t_pow = time.perf_counter() - t0
+        out.update(powerurv_s=t_pow, powerurv_rate=f_pow / t_pow, powerurv_gflop=f_pow / 1e9)
+    else:
+        out.update(powerurv_s=0.0, powerurv_rate=pow_rate, powerurv_gflop=0.0)
+    return out
+
+
+def cpu_extrapolate(r, n, b, q):
+    """Seconds of one randUTV + powerURV step at n x n at the sampled rates (flop model)."""
+    from paper_2106_13402_gb300 import testmats
+    return testmats.flops_randutv(n, n, b, q) / r["randutv_rate"] + testmats.flops_powerurv(n, n, q) / r["powerurv_rate"]
+
+
+def cpu_sample_text(r, n, b, q, pow_n):
+    return (f"randUTV: its first step (of {n // b}) on the same {n}x{n} matrix, {r['randutv_gflop']:.0f} GFLOP in "
+            f"{r['randutv_s']:.1f} s ({r['randutv_rate'] / 1e9:.2f} GFLOP/s); powerURV: in full on a {pow_n}x{pow_n} "
+            f"matrix of the same recipe ({r['powerurv_rate'] / 1e9:.2f} GFLOP/s); each rate extrapolated to the "
+            f"{n}x{n} method by the flop model")
+
+
+def cpu_sample(A_np, n, b, q, pow_n):
+    import oracle
+    r = cpu_rates(A_np, n, b, q, pow_n)
+    per_step_s = cpu_extrapolate(r, n, b, q)
+    return {"value": 2.0 / per_step_s, "unit": "factorizations/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": cpu_sample_text(r, n, b, q, pow_n), "extrapolated": True,
+            "seconds": round(r["randutv_s"] + r["powerurv_s"], 2)}
 
 
 def power_norm(torch, M, iters=60):
@@ -191,6 +242,89 @@ def power_norm(torch, M, iters=60):
 
 
 # ------------------------------------------------------------------------------------------ our arm --
+def _event_ms(torch, fn, stream):
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    fn()
+    a1.record(stream)
+    a1.synchronize()
+    return a0.elapsed_time(a1)
+
+
+def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
+    """Read the GEMM event profiler (after rrf_gemm_profile_end) and describe the dominant kernel."""
+    gemm_ms, gemm_flops, gemm_launches = rrf.gemm_profile_end()
+    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    if emu_ms > gemm_ms:
+        # the emulated GEMM's tensor-core kernel (BF16 digit products, timed inside a long step -> the
+        # sustained BF16 peak)
+        achieved = emu_tflops / (emu_ms / 1e3) / 1e12
+        peak = float(peaks["bf16_tflops_sustained"])
+        traffic, tsrc = ozaki_traffic("step_8192")
+        return {"kernel": "ozaki_gemm_kernel (FP64 product emulated with 7 BF16 digit slices)", "bound": "tensor",
+                "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "traffic_source": tsrc,
+                "traffic_unit": "DRAM bytes read + written per launch, averaged over the launches of one step",
+                "peak_source": f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
+                "work": "28 digit-pair products x 2 M N K' BF16 flops per launch (K' = K rounded up to 32)",
+                "fp64_equivalent_tflops": round(emu_flops / (emu_ms / 1e3) / 1e12, 3),
+                "launches": int(emu_launches), "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),
+                "share_of_step": round(emu_ms / (ms_step * steps), 4),
+                "dfma_gemm": {"ms": round(gemm_ms, 1), "launches": int(gemm_launches),
+                              "tflops": round(gemm_flops / (gemm_ms / 1e3) / 1e12, 4) if gemm_ms > 0 else 0.0}}
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+    return {"kernel": "gemm_f64_kernel (+ split-K reduction)", "bound": "alu", "achieved": round(achieved, 4),
+            "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+            "traffic": None, "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; recipe nominal 1.25)",
+            "launches": int(gemm_launches), "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4),
+            "share_of_step": round(gemm_ms / (ms_step * steps), 4)}
+
+
+def extras_8192(torch, rrf, testmats, A, s, dev, n, b):
+    """Sub-results for the configurations the speed-up target is set on, on the same 8192^2 matrix:
+    (1) learned per-step q with the BF16 sketch (fallback q = 2) against the plain FP64 method with q = 2;
+    (2) randUTV_boosted (Algorithm 2, q = 2, p = b) against the same algorithm with every product on the
+    DFMA pipe.  One warm run and one timed run each; e_k / sigma_{k+1} at every block boundary."""
+    from paper_2106_13402_gb300 import qpolicy
+    ks = list(range(b, n, b))
+    steps = n // b
+    out = (rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev), rrf.fortran_empty(n, n, dev))
+    stream = torch.cuda.current_stream()
+    on_target = lambda r: sum(1 for v in r.values() if v <= 1.1)
+
+    def timed(opts):
+        ws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, opts), dev)
+        rrf.randutv(A, b, 2, 17, opts=opts, ws=ws, out=out)
+        t = _event_ms(torch, lambda: rrf.randutv(A, b, 2, 17, opts=opts, ws=ws, out=out, check_status=False), stream)
+        st = rrf.lib().rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None))
+        r = _boundary_ratios(torch, out[1], s, b, ks)
+        del ws
+        return t, r, int(st)
+
+    res = {}
+    pms, r_plain, _ = timed(rrf.make_opts(gemm_mode=rrf.GEMM_NATIVE))
+    params = qpolicy.load(str(dev))
+    if params is not None:
+        fast = rrf.make_opts(sketch_prec=rrf.SKETCH_BF16, q_policy=rrf.Q_LEARNED, mlp_params=params, steps=steps)
+        fms, r_fast, st = timed(fast)
+        qs = rrf.opts_q_used(fast)[: steps - 1]
+        res["learned_q_bf16_sketch"] = {
+            "ms": round(fms, 1), "speedup_vs_plain_fp64_q2": round(pms / fms, 3), "plain_fp64_q2_ms": round(pms, 1),
+            "on_target": on_target(r_fast), "plain_on_target": on_target(r_plain), "boundaries": len(ks),
+            "max_ratio": max(r_fast.values()), "plain_max_ratio": max(r_plain.values()),
+            "q_used": {"mean": round(sum(qs) / len(qs), 3), "hist": [qs.count(v) for v in range(4)]},
+            "device_status": st}
+    bms, r_boost, st = timed(rrf.make_opts(oversample=b))
+    bpms, r_bplain, _ = timed(rrf.make_opts(oversample=b, gemm_mode=rrf.GEMM_NATIVE))
+    res["boosted_q2_p128"] = {
+        "ms": round(bms, 1), "speedup_vs_plain_fp64_boosted": round(bpms / bms, 3), "plain_fp64_boosted_ms": round(bpms, 1),
+        "speedup_vs_plain_fp64_basic_q2": round(pms / bms, 3),
+        "on_target": on_target(r_boost), "boundaries": len(ks), "max_ratio": max(r_boost.values()),
+        "device_status": st}
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -242,12 +376,12 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
+    # Timed region: K steps, nothing else enqueued (no profiler events).
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     l0 = rrf.launch_count()
-    rrf.gemm_profile_begin(200000)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -255,8 +389,6 @@ def run_ours(args):
         step()
     e1.record(stream)
     e1.synchronize()
-    gemm_ms, gemm_flops, gemm_launches = rrf.gemm_profile_end()
-    emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
     launches = rrf.launch_count() - l0
     clocks = sampler.stop()
     torch.cuda.synchronize()
@@ -266,40 +398,40 @@ def run_ours(args):
         (testmats.flops_powerurv(n, n, q) if "powerurv" in methods else 0.0)
     value = replica_rate(len(methods), world, ms)
 
+    # Profiled pass: the same step with CUDA events around every GEMM launch on its stream, for the
+    # dominant kernel's roofline; its step time is reported beside the headline's.
+    prof_steps = max(1, min(args.steps, 3))
+    rrf.gemm_profile_begin(200000)
+    pms_step = _event_ms(torch, lambda: [step() for _ in range(prof_steps)], stream) / prof_steps
+    peaks, peak_src = measured_peaks()
+    roof = dominant_kernel_roofline(rrf, pms_step, prof_steps, peaks, peak_src)
+    roof["measured_over"] = (f"a profiled pass of {prof_steps} steps after the timed region "
+                             f"({pms_step:.1f} ms per step with the event profiler on, {ms:.1f} without)")
+
     # Per-method device times (one more run each, outside the timed region).
     per = {}
     for name in ([] if args.no_per_method else methods):
         f = testmats.flops_randutv(n, n, b, q) if name == "randutv" else testmats.flops_powerurv(n, n, q)
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        getattr(rrf, name)(A, b, q, seed=17, opts=opts, out=outs[name], ws=wss[name], check_status=False)
-        a1.record(stream)
-        a1.synchronize()
-        t = a0.elapsed_time(a1)
+        t = _event_ms(torch, lambda: getattr(rrf, name)(A, b, q, seed=17, opts=opts, out=outs[name], ws=wss[name],
+                                                        check_status=False), stream)
         per[name] = {"ms": round(t, 1), "tflops": round(f / t / 1e9, 4), "gflop": round(f / 1e9, 1)}
 
-    # The plain FP64 method (every product on the DFMA pipe) on the same GPU, one run per method.
+    # The plain FP64 method (every product on the DFMA pipe) on the same GPU, --plain-reps runs per method.
     plain = None
     if not args.no_plain and args.gemm != "native":
         popts = rrf.make_opts(gemm_mode=rrf.GEMM_NATIVE)
-        pms = 0.0
         pper = {}
         for name in methods:
             pws = rrf.workspace((rrf.randutv_workspace_bytes if name == "randutv" else rrf.powerurv_workspace_bytes)(
                 n, n, b, popts), dev)
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            getattr(rrf, name)(A, b, q, seed=17, opts=popts, out=outs[name], ws=pws, check_status=False)
-            a1.record(stream)
-            a1.synchronize()
-            t = a0.elapsed_time(a1)
-            pper[name] = round(t, 1)
-            pms += t
+            runs = [_event_ms(torch, lambda: getattr(rrf, name)(A, b, q, seed=17, opts=popts, out=outs[name], ws=pws,
+                                                                 check_status=False), stream)
+                    for _ in range(max(1, args.plain_reps))]
+            pper[name] = {"median_ms": round(statistics.median(runs), 1), "runs_ms": [round(x, 1) for x in runs]}
             del pws
+        pms = sum(v["median_ms"] for v in pper.values())
         plain = {"gemm": "native (DFMA)", "ms_per_step": round(pms, 1), "value": round(len(methods) / (pms / 1e3), 5),
-                 "per_method_ms": pper, "speedup_of_value": round((len(methods) / (ms / 1e3)) / (len(methods) / (pms / 1e3)), 3)}
+                 "per_method": pper, "speedup_of_value": round((len(methods) / (ms / 1e3)) / (len(methods) / (pms / 1e3)), 3)}
         # restore the default path's outputs for the accuracy check below
         for name in methods:
             getattr(rrf, name)(A, b, q, seed=17, opts=opts, out=outs[name], ws=wss[name], check_status=False)
@@ -338,41 +470,20 @@ def run_ours(args):
                     "max_ratio": max(ratios.values()) if ratios else None, "boundaries": len(ratios),
                     "on_target": sum(1 for v in ratios.values() if v <= 1.1)}
 
+    extras = None
+    if not args.no_extras and world == 1 and n == 8192 and b == 128:
+        del wss
+        extras = extras_8192(torch, rrf, testmats, A, s, dev, n, b)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_sample(np.asfortranarray(A.cpu().numpy()), n, b, q, args.cpu_sample_steps)
+        cpu = cpu_sample(np.asfortranarray(A.cpu().numpy()), n, b, q, args.cpu_pow_n)
 
-    peaks, peak_src = measured_peaks()
-    if emu_ms > gemm_ms:
-        # dominant kernel: the emulated GEMM's tensor-core kernel (BF16 digit products, timed inside a long
-        # step -> the sustained BF16 peak)
-        achieved = emu_tflops / (emu_ms / 1e3) / 1e12
-        peak = float(peaks["bf16_tflops_sustained"])
-        roof = {"kernel": "ozaki_gemm_kernel (FP64 product emulated with 7 BF16 digit slices)", "bound": "tensor",
-                "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
-                "work": "28 digit-pair products x 2 M N K' BF16 flops per launch (K' = K rounded up to 32)",
-                "fp64_equivalent_tflops": round(emu_flops / (emu_ms / 1e3) / 1e12, 3),
-                "launches": int(emu_launches), "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),
-                "share_of_step": round(emu_ms / (ms * args.steps), 4),
-                "dfma_gemm": {"ms": round(gemm_ms, 1), "launches": int(gemm_launches),
-                              "tflops": round(gemm_flops / (gemm_ms / 1e3) / 1e12, 4) if gemm_ms > 0 else 0.0}}
-    else:
-        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
-        roof = {"kernel": "gemm_f64_kernel (+ split-K reduction)", "bound": "alu", "achieved": round(achieved, 4),
-                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": None,
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; recipe nominal 1.25)",
-                "launches": int(gemm_launches), "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4),
-                "share_of_step": round(gemm_ms / (ms * args.steps), 4)}
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "factorizations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": methods, "gemm": args.gemm,
-                   "seeds": {"Q1": 11, "Q2": 12, "G": 17}, "l2": "inputs larger than L2 (A is 512 MB)",
-                   "parallelism": f"replicas x{world}"},
+        "config": config_c2(n, b, q, methods, args.gemm, world),
         "tflops": round(world * flops / (ms / 1e3) / 1e12, 4),
         "per_method": per,
         "clocks": clocks,
@@ -382,6 +493,7 @@ def run_ours(args):
         "roofline": roof,
         "plain_fp64": plain,
         "accuracy": accuracy,
+        "target_configs": extras,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -390,10 +502,21 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def config_c2(n, b, q, methods, gemm, world):
+    """The workload description both arms print (identical for the same arguments)."""
+    return {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": methods, "gemm": gemm,
+            "seeds": {"Q1": 11, "Q2": 12, "G": 17}, "l2": "inputs larger than L2 (A is 512 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
 # ------------------------------------------------------------------------------------ reference arm --
 def run_reference(args):
-    """The oracle (plain FP64 CPU implementation of the method), timed on the host cores on a bounded
-    sample of the same workload per step."""
+    """The oracle (the plain FP64 CPU implementation of the method, as it stands) on the host cores.  Each
+    step is a bounded sample of the workload: randUTV's first block step on the same 8192^2 matrix, timed
+    through the oracle's entry point (the same work the first step of our randUTV does).  powerURV is timed
+    once, in full, on a --cpu-pow-n matrix of the same recipe.  value extrapolates the measured rates to one
+    randUTV + powerURV step of the full workload by the flop model; ms_per_step is the measured wall time
+    of one sample step."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -413,21 +536,32 @@ def run_reference(args):
             del A_t
         else:
             A, s = testmats.make_matrix(n, n, "c2", 11, 12, device="cpu")
-    samples = []
+    # warm-up: the oracle's thread pool and pages, on a small matrix (untimed)
+    Aw, _ = testmats.make_matrix(256, 256, "c2", 11, 12, device="cpu")
     for _ in range(args.warmup):
-        cpu_sample(A, n, b, q, 1)
+        oracle.randutv(Aw, b, q, seed=17, max_steps=1)
+    pow_r = cpu_rates(A, n, b, q, args.cpu_pow_n)   # also gives powerURV's rate (timed once)
+    samples = []
+    t_all = time.perf_counter()
     for _ in range(args.steps):
-        samples.append(cpu_sample(A, n, b, q, 1))
-    per_step_s = statistics.mean(2.0 / x["value"] for x in samples)
+        samples.append(cpu_rates(A, n, b, q, args.cpu_pow_n, pow_rate=pow_r["powerurv_rate"]))
+    wall = time.perf_counter() - t_all
+    rate = statistics.mean(x["randutv_rate"] for x in samples)
+    r = dict(samples[-1], randutv_rate=rate, powerurv_rate=pow_r["powerurv_rate"], powerurv_s=pow_r["powerurv_s"],
+             powerurv_gflop=pow_r["powerurv_gflop"])
+    per_step_s = cpu_extrapolate(r, n, b, q)
     value = 2.0 / per_step_s
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 7), "unit": "factorizations/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_s * 1e3, 1),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": n, "n": n, "b": b, "q": q, "methods": ["randutv", "powerurv"],
-                   "seeds": {"Q1": 11, "Q2": 12, "G": 17}, "l2": "host run", "parallelism": "host cores"},
+        "config": config_c2(n, b, q, ["randutv", "powerurv"], "auto", world),
+        "extrapolated": True,
+        "sample_steps_run": args.steps,
+        "extrapolated_s_per_workload_step": round(per_step_s, 1),
+        "powerurv_calibration_s": round(pow_r["powerurv_s"], 2),
         "cpu_baseline": {"value": round(value, 7), "unit": "factorizations/s", "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": samples[-1]["sample"]},
+                         "kind": "oracle", "sample": "each step: " + cpu_sample_text(r, n, b, q, args.cpu_pow_n)},
         "e2e": {"value": round(value, 7), "unit": "factorizations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -725,7 +859,8 @@ def run_gemm(args):
         "data": "synthetic", "config": {"workload": "C = A B, A and B 4096 x 4096 N(0,1) FP64", "l2": "inputs 256 MB, larger than L2"},
         "clocks": clocks, "gpu_launches": None,
         "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": GEMM_4096_DRAM_BYTES,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ozaki_traffic("gemm_4096")[0],
+                     "traffic_source": ozaki_traffic("gemm_4096")[1],
                      "traffic_unit": "bytes per launch (dram read + write, ncu)",
                      "algorithmic_bytes": 2 * 7 * m * k * 2 + 8 * m * n,
                      "peak_source": f"{peak_src} bf16_tflops (burst)", "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),

@@ -64,7 +64,7 @@ def test_randutv_bf16_sketch(m, n, b, q, prof):
     assert np.abs(U.T @ U - np.eye(m)).max() <= 1e-12
     assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
     assert np.all(np.tril(T, -1) == 0.0)
-    Uo, To, Vo, st = oracle.randutv(A, b, q, seed=99)
+    Uo, To, Vo, st = oracle.randutv_reorth(A, b, q, 99)   # the FP64 form of the same (re-orthonormalized) sketch
     rg, ro = _ratios(T, s, b, n), _ratios(To, s, b, n)
     assert np.all(rg >= 1 - 1e-10)
     # Rounding T22 to BF16 perturbs it by up to 2^-9 ||T22||_F, which shifts the sampled subspace by a
