@@ -86,4 +86,5 @@ def test_jacobi_sweep_cap_reports_not_converged():
         assert st == rrf.RRF_NOT_CONVERGED, c
         Us, s, Vs, st = rrf.jacobi_svd(dev(M))
         assert st == rrf.RRF_OK
-        np.testing.assert_allclose(host(s), np.linalg.svd(M, compute_uv=False), rtol=1e-12)
+        sv = np.linalg.svd(M, compute_uv=False)
+        np.testing.assert_allclose(host(s), sv, rtol=1e-12, atol=1e-14 * sv[0])
