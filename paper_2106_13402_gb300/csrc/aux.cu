@@ -126,7 +126,18 @@ cudaError_t frob_launch(int64_t rows, int64_t cols, const double* X, int64_t ld,
   return cudaGetLastError();
 }
 
+__global__ void merge_status_kernel(int* dst, const int* src) {
+  const int v = *(volatile const int*)src;
+  if (v != 0) atomicCAS(dst, 0, v);
+}
+
 }  // namespace
+
+cudaError_t merge_status(int* dst, const int* src, cudaStream_t s) {
+  merge_status_kernel<<<1, 1, 0, s>>>(dst, src);
+  count_launch();
+  return cudaGetLastError();
+}
 
 size_t frob_scratch_bytes() { return kSumsqMaxBlocks * sizeof(double); }
 

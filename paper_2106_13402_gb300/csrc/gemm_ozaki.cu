@@ -7,22 +7,23 @@
 // as S = 7 signed base-256 digits per entry:  a = 2^e_r sum_s d_s 2^-8(s+1) + rem,  |d_s| <= 128,
 // |rem| <= 2^-57 2^e_r < 2^-55 max_k |a_rk| -- every digit an exact BF16 value and every step exact in FP64.
 // Columns of op(B) likewise (exponents f_c).
-// Products: a digit product is at most 2^14, so over a 32-wide K chunk the diagonal sum
-// S_d = sum_{i+j=d} sum_k d^A_i d^B_j (d + 1 pairs) is an integer of magnitude <= (d + 1) 2^19 <= 2^22: the
-// tcgen05 MMA's FP32 accumulation is exact, and so is the conversion of each S_d to an integer (x + 1.5 2^23
-// holds round(x) in its low mantissa bits).  The epilogue adds S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4
-// into one int64 per output (exact; a split covers at most 65536 of K, so it stays below 2^63) and the
-// remaining S_5 2^-8 + S_6 2^-16 into an FP32 fraction whose integer part moves into the int64 after every
-// chunk (its rounding is below 2^-60 of the row/column scale per chunk).  The digit products of diagonals
-// 7..12 are dropped (at most 2^-51.4 max|a_r.| max|b_.c| per k, ~2^-56 for random digits).  At the end
-// C = alpha 2^(e_r + f_c - 48) (acc + frac) + beta C in FP64.
+// Products: a digit product is at most 2^14, so over 64 of K the diagonal sum
+// S_d = sum_{i+j=d} sum_k d^A_i d^B_j (d + 1 pairs) is an integer of magnitude <= (d + 1) 2^20 < 2^23: the
+// tcgen05 MMA's FP32 accumulation is exact.  S_0 .. S_3 (<= 2^22) convert to integers exactly by a
+// magic-number add (x + 1.5 2^23 holds round(x) in its low mantissa bits), S_4 by a round-to-nearest
+// conversion instruction.  The epilogue adds S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 into one int64
+// per output (exact; a split covers at most 65536 of K, so it stays below 2^63) and the remaining
+// S_5 2^-8 + S_6 2^-16 into an FP32 fraction whose integer part moves into the int64 after every read (its
+// rounding is below 2^-59 of the row/column scale per read).  The digit products of diagonals 7..12 are
+// dropped (at most 2^-51.4 max|a_r.| max|b_.c| per k, ~2^-56 for random digits).  At the end
+// C = alpha 2^(e_r + f_c - 48) (acc + frac) + beta C, the FP64 value packed with integer instructions.
 //
 // Kernel (576 threads, persistent over 128 x 32 output tiles x K splits): warp 0 lane 0 loads the 7 + 7
-// digit tiles of each 32-wide K chunk with two 3-D TMA loads (64-byte swizzle, 3-stage ring); warp 1 lane 0 issues, per
-// 16-wide K step and A digit a, one MMA of A_a against the B digits 0..6-a laid back to back (N = (7-a) 32),
-// into two TMEM accumulator buffers of 7 x 32 columns used alternately; warps 2..17 read a buffer
-// (tcgen05.ld) while the MMAs fill the other.  All mbarrier waits are bounded (RRF_TIMEOUT, drain, free
-// TMEM, exit).
+// digit tiles of each 32-wide K chunk with two 3-D TMA loads (64-byte swizzle, 3-stage ring); warp 1 lane 0
+// issues, per 16-wide K step and A digit a, one MMA of A_a against the B digits 0..6-a laid back to back
+// (N = (7-a) 32), accumulating two chunks (64 of K) into one of two TMEM buffers of 7 x 32 columns used
+// alternately; warps 2..17 read a buffer (tcgen05.ld) while the MMAs fill the other.  All mbarrier waits
+// are bounded (RRF_TIMEOUT, drain, free TMEM, exit).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -38,6 +39,7 @@ constexpr int kS = 7;            // digits per value
 constexpr int BM = 128, BN = 32;
 constexpr int KC = 32;           // K per chunk / stage (64 bytes of BF16: 64-byte swizzle)
 constexpr int kStages = 3;
+constexpr int kHarvest = 2;      // chunks accumulated in TMEM per epilogue read (64 of K)
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kBufCols = 256;    // TMEM columns between the two accumulator buffers (7 x BN = 224 used)
@@ -62,6 +64,7 @@ struct OzParams {
   int64_t ldc;
   int ct;               // write C^T: element (row, col) at C[col + row ldc]
   int* status;
+  int amode;            // alpha: 1 -> +1, 2 -> -1, 0 -> any other value
   long long stall_cycles;  // failure injection only (0 normally): the MMA warp first waits this long on a
                            // barrier nothing arrives on, then aborts
 };
@@ -152,6 +155,36 @@ __device__ __forceinline__ int exact_int(uint32_t bits) {
   return __float_as_int(__fadd_rn(__uint_as_float(bits), kMagic)) - kMagicBits;
 }
 
+// (acc + ta) 2^x as an FP64 value, for an exact integer acc and a fraction |ta| <= 1/2, with integer
+// instructions only: this GPU's FP64 pipe does ~2 operations per clock per SM, far too few for a
+// conversion, an add and a scaling per output.  The fixed-point value W = acc 2^10 + round(ta 2^10) (acc
+// alone once |acc| >= 2^52, where the fraction is below the result's precision) is rounded to 53 bits,
+// to nearest even, and packed with its exponent.  Subnormal or overflowing results take the FP64 path.
+__device__ __forceinline__ double fixed_to_double(long long acc, float ta, int x) {
+  const unsigned long long aa = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+  long long W = acc;
+  int xs = x;
+  if (aa < (1ull << 52)) {
+    W = acc * 1024 + exact_int(__float_as_uint(ta * 1024.f));  // |ta 2^10| <= 2^9: exact rounding
+    xs = x - 10;
+  }
+  if (W == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)W & 0x8000000000000000ull;
+  const unsigned long long mag = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const int lz = __clzll((long long)mag);
+  const unsigned long long top = mag << lz;  // leading one at bit 63
+  unsigned long long m = top >> 11;          // 53 significant bits
+  const unsigned long long rem = top & 0x7FFull;
+  m += (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+  int e = 63 - lz + xs;                      // exponent of the leading bit
+  if (m >> 53) {
+    m >>= 1;
+    ++e;
+  }
+  if (e < -1022 || e > 1023) return ldexp((double)W, xs);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
 // Persistent kernel: each CTA walks work units blockIdx.x, blockIdx.x + gridDim.x, ...  The 32-wide K
 // chunks of all its units form one stream g = 0, 1, ...: chunk g uses smem stage g % kStages and TMEM
 // accumulator buffer g % 2, so the MMAs of chunk g + 1 run while the epilogue folds chunk g.
@@ -227,8 +260,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // One MMA per A digit a per 16-wide K step: D[a .. 6] += A_a [B_0 .. B_{6-a}]^T.  The B digit tiles sit
       // back to back in shared memory, so they form one K-major operand of N = (7 - a) BN rows whose
       // products land on the diagonals a + j, stored contiguously in TMEM (diagonal d at column d BN).
+      // Round h accumulates kHarvest chunks (64 of K) into TMEM buffer h % 2 before the epilogue reads it.
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
-      int64_t g = 0;
+      int64_t g = 0, h = 0;  // chunks consumed (shared-memory ring), rounds committed (TMEM ring)
       bool run = true;
       if (p.stall_cycles > 0 && !mbar_wait_for(&never_bar, 0, p.stall_cycles)) {
         set_status(p.status, RRF_TIMEOUT);
@@ -240,35 +274,50 @@ __global__ void __launch_bounds__(kThreads, 1)
         int split;
         unit_coords(p, u, m0, n0, split);
         const int nch = unit_chunks(p, split, k0);
-        for (int i = 0; i < nch; ++i, ++g) {
-          const int s = (int)(g % kStages);
-          const int bf = (int)(g & 1);
-          if (!mbar_wait(&full_bar[s], (uint32_t)(g / kStages) & 1) ||
-              (g >= 2 && !mbar_wait(&acc_empty[bf], (uint32_t)((g >> 1) - 1) & 1))) {
+        for (int c0 = 0; c0 < nch && run; c0 += kHarvest) {
+          const int bf = (int)(h & 1);
+          if (h >= 2 && !mbar_wait(&acc_empty[bf], (uint32_t)((h >> 1) - 1) & 1)) {
             set_status(p.status, RRF_TIMEOUT);
             atomicExch(&abort_flag, 1);
             run = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          unsigned char* st = smem + s * kStageBytes;
-          const uint64_t db = smem_desc_sw64(st + kS * kTileA);
-#pragma unroll
-          for (int kk = 0; kk < KC / 16; ++kk) {
-#pragma unroll
-            for (int a = 0; a < kS; ++a) {
-              const uint64_t da = smem_desc_sw64(st + a * kTileA);
-              const uint32_t idesc = idesc0 | ((uint32_t)(((kS - a) * BN) >> 3) << 17);
-              mma_bf16(tmem + (uint32_t)(bf * kBufCols + a * BN), da + 2 * kk, db + 2 * kk, idesc,
-                       (a > 0 || kk > 0) ? 1u : 0u);
+          const int c1 = min(nch, c0 + kHarvest);
+          bool issued_any = false;
+          for (int i = c0; i < c1; ++i, ++g) {
+            const int s = (int)(g % kStages);
+            if (!mbar_wait(&full_bar[s], (uint32_t)(g / kStages) & 1)) {
+              set_status(p.status, RRF_TIMEOUT);
+              atomicExch(&abort_flag, 1);
+              run = false;
+              break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char* st = smem + s * kStageBytes;
+            const uint64_t db = smem_desc_sw64(st + kS * kTileA);
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+#pragma unroll
+              for (int a = 0; a < kS; ++a) {
+                const uint64_t da = smem_desc_sw64(st + a * kTileA);
+                const uint32_t idesc = idesc0 | ((uint32_t)(((kS - a) * BN) >> 3) << 17);
+                mma_bf16(tmem + (uint32_t)(bf * kBufCols + a * BN), da + 2 * kk, db + 2 * kk, idesc,
+                         (i > c0 || a > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+            mma_commit(&empty_bar[s]);
+            issued_any = true;
           }
-          mma_commit(&empty_bar[s]);
-          mma_commit(&acc_full[bf]);
+          // commit the round (also a partial one cut short by a timeout, so that the wait below covers
+          // every MMA issued before TMEM is released)
+          if (issued_any) {
+            mma_commit(&acc_full[bf]);
+            ++h;
+          }
         }
       }
       // the last MMAs must finish before TMEM is released
-      if (g > 0) mbar_wait(&acc_full[(g - 1) & 1], (uint32_t)((g - 1) >> 1) & 1);
+      if (h > 0) mbar_wait(&acc_full[(h - 1) & 1], (uint32_t)((h - 1) >> 1) & 1);
     }
   } else {
     // Epilogue warps ew = 0..15: TMEM lane quadrant (warp % 4) = 32 tile rows, columns 8 (ew / 4) .. +7.
@@ -276,22 +325,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quad = warp & 3;
     const int col0 = (ew >> 2) * 8;
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
-    int64_t g = 0;
+    int64_t h = 0;
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
       int64_t m0, n0, k0;
       int split;
       unit_coords(p, u, m0, n0, split);
       const int nch = unit_chunks(p, split, k0);
-      // acc: sum over chunks of S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 (exact); ta: the rest,
-      // S_5 2^-8 + S_6 2^-16, in the same unit, with its integer part moved into acc after every chunk.
+      // acc: sum over rounds of S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 (exact); ta: the rest,
+      // S_5 2^-8 + S_6 2^-16, in the same unit, with its integer part moved into acc after every round.
       long long acc[8];
       float ta[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) { acc[c] = 0; ta[c] = 0.f; }
       bool ok = true;
-      for (int i = 0; i < nch; ++i, ++g) {
-        const int bf = (int)(g & 1);
-        if (!mbar_wait(&acc_full[bf], (uint32_t)(g >> 1) & 1)) {
+      for (int c0 = 0; c0 < nch; c0 += kHarvest, ++h) {
+        const int bf = (int)(h & 1);
+        if (!mbar_wait(&acc_full[bf], (uint32_t)(h >> 1) & 1)) {
           set_status(p.status, RRF_TIMEOUT);
           atomicExch(&abort_flag, 1);
           ok = false;
@@ -308,15 +357,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&acc_empty[bf]);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          // |S_d| <= (d + 1) 32 2^14 <= 2^22 for every diagonal: each converts exactly.
-          const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^28
+          // Over a round of 64 of K, |S_d| <= (d + 1) 64 2^14: S_0 .. S_3 are within 2^22 and convert exactly
+          // by the magic-number add; S_4 (up to 5 2^20) by a round-to-nearest conversion instruction.
+          const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^29
           const int mid = exact_int(v[2][c]) * 256 + exact_int(v[3][c]);  // |.| < 2^30
+          const int d4 = __float2int_rn(__uint_as_float(v[4][c]));
           float t = fmaf(__uint_as_float(v[5][c]), 0.00390625f, ta[c]);
           t = fmaf(__uint_as_float(v[6][c]), 1.52587890625e-05f, t);
           const float r = __fadd_rn(t, kMagic);
           const int ti = __float_as_int(r) - kMagicBits;
           ta[c] = __fsub_rn(t, __fsub_rn(r, kMagic));
-          acc[c] += (long long)hi * 16777216LL + (long long)mid * 256LL + (long long)(exact_int(v[4][c]) + ti);
+          acc[c] += (long long)hi * 16777216LL + (long long)mid * 256LL + (long long)(d4 + ti);
         }
       }
       if (!ok || *(volatile int*)&abort_flag) break;
@@ -327,13 +378,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < 8; ++c) {
         const int64_t col = n0 + col0 + c;
         if (col >= p.N) continue;
-        // value = 2^(e_r + f_c) sum_d S_d 2^-8(d+2) = (acc + ta) 2^(e_r + f_c - 48)
-        const double v = nch > 0 ? ldexp((double)acc[c] + (double)ta[c], er + p.eb[col] - 48) : 0.0;
+        // value = 2^(e_r + f_c) sum_d S_d 2^-8(d+2) = (acc + ta) 2^(e_r + f_c - 48), assembled with integer
+        // instructions; alpha = +-1 is a sign change, other alpha one FP64 multiply, beta != 0 one FP64 FMA.
+        double v = nch > 0 ? fixed_to_double(acc[c], ta[c], er + p.eb[col] - 48) : 0.0;
         if (p.splits == 1) {
           double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
-          double out = p.alpha * v;
-          if (p.beta != 0.0) out = fma(p.beta, *cp, out);
-          *cp = out;
+          if (p.amode == 2) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+          else if (p.amode == 0) v = p.alpha * v;
+          if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+          *cp = v;
         } else {
           p.C[((int64_t)split * p.N + col) * p.M + row] = v;
         }
@@ -532,7 +585,7 @@ cudaError_t gemm_run(const GemmEngine& eng, const GemmDesc* d, int count, cudaSt
         ct = true;
       }
       if (ozaki_scratch_bytes(e.M, e.N, e.K) <= eng.oz_bytes) {
-        cudaError_t err = gemm_ozaki(e, ct, eng.oz, eng.oz_bytes, eng.status, s);
+        cudaError_t err = gemm_ozaki(e, ct, eng.oz, eng.oz_bytes, eng.status, s, eng.max_ctas);
         if (err != cudaSuccess) return err;
         continue;
       }
@@ -553,7 +606,7 @@ size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K) {
 }
 
 cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, size_t scratch_bytes, int* status,
-                       cudaStream_t s) {
+                       cudaStream_t s, int max_ctas) {
   if (d.M <= 0 || d.N <= 0) return cudaSuccess;
   const int64_t M = d.M, N = d.N, K = d.K;
   const int64_t Kp = (K + KC - 1) / KC * KC;
@@ -607,13 +660,14 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   p.units = (int64_t)p.tiles_m * p.tiles_n * splits;
   p.ea = ea; p.eb = eb;
   p.alpha = d.alpha; p.beta = d.beta;
+  p.amode = d.alpha == 1.0 ? 1 : (d.alpha == -1.0 ? 2 : 0);
   p.C = splits == 1 ? d.C : part;
   p.ldc = d.ldc;
   p.ct = out_transposed ? 1 : 0;
   p.status = status;
   const Inject inj = inject_state();
   p.stall_cycles = inj.kind == RRF_INJECT_GEMM_STALL ? inj.value : 0;
-  const unsigned grid = (unsigned)std::min<int64_t>(p.units, sms);
+  const unsigned grid = (unsigned)std::min<int64_t>(p.units, max_ctas > 0 ? std::min(max_ctas, sms) : sms);
   // profiled work: the FP64 product's 2 M N K, and the tensor work 28 x 2 M N Kp of the digit products
   cudaEvent_t ev_end = profile_launch_begin(1, 2.0 * M * N * K, 56.0 * M * N * Kp, s);
   ozaki_gemm_kernel<<<grid, kThreads, oz_smem(), s>>>(ma, mb, p);

@@ -486,6 +486,9 @@ size_t jacobi_smem(int c, int cl, bool pre) {
   return b + 2 * kMaxC * sizeof(double) + kMaxC * sizeof(int);
 }
 
+// Largest c a cluster of CL CTAs takes: two CTAs hold c <= 128 (rows of M and V in ~150 KB each).
+constexpr int max_c_for(int CL) { return CL >= 8 ? kMaxC : 128; }
+
 template <int CL, bool PRE>
 cudaError_t set_jacobi_attrs() {
   if (CL > 8) {
@@ -493,7 +496,7 @@ cudaError_t set_jacobi_attrs() {
     if (e != cudaSuccess) return e;
   }
   return cudaFuncSetAttribute(jacobi_kernel<CL, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)jacobi_smem(kMaxC, CL, PRE));
+                              (int)jacobi_smem(max_c_for(CL), CL, PRE));
 }
 
 // 16-CTA clusters are not portable: use them when the device accepts the attribute and can schedule one.
@@ -558,13 +561,14 @@ size_t jacobi_scratch_bytes(int64_t c) {
 
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch,
-                       size_t scratch_bytes) {
+                       size_t scratch_bytes, bool narrow) {
   if (c <= 0) return cudaSuccess;
   if (c > kMaxC) return cudaErrorInvalidValue;
   JacobiArgs a;
   a.c = (int)c;
-  // 16 CTAs only pay off when each holds enough rows (c > 128); measured on GB300
-  const int cl = (c > 128) ? jacobi_cluster_size() : 8;
+  // 16 CTAs only pay off when each holds enough rows (c > 128); measured on GB300.  `narrow` asks for the
+  // fewest SMs (2 for c <= 128), for an SVD that runs beside other work.
+  const int cl = (c > 128) ? jacobi_cluster_size() : (narrow ? 2 : 8);
   a.rp = (int)((c + cl - 1) / cl);
   a.M = M;
   a.ldm = ldm;
@@ -606,7 +610,7 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
       pa.Vs = X;
       pa.ldv = c;
       pa.V0 = nullptr;
-      e = (cl == 16) ? launch_jacobi<16, true>(pa, (int)c, stream) : launch_jacobi<8, true>(pa, (int)c, stream);
+      e = (cl == 16) ? launch_jacobi<16, true>(pa, (int)c, stream) : launch_jacobi<8, true>(pa, (int)c, stream);  // c > 128
       if (e == cudaSuccess) e = cudaGetLastError();
     }
     count_launch();
@@ -643,7 +647,8 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   }
   e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  e = (cl == 16) ? launch_jacobi<16, false>(a, (int)c, stream) : launch_jacobi<8, false>(a, (int)c, stream);
+  e = (cl == 16) ? launch_jacobi<16, false>(a, (int)c, stream)
+                  : (cl == 2 ? launch_jacobi<2, false>(a, (int)c, stream) : launch_jacobi<8, false>(a, (int)c, stream));
   count_launch();
   if (e != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

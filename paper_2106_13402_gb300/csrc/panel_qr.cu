@@ -12,8 +12,7 @@
 // workspace status word instead of hanging.
 //
 // The compact-WY factor (Schreiber & Van Loan) is built from the Gram matrix S = Y^T Y (through the
-// caller's GEMM router when given) by the forward recurrence Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j),
-// Tf(j, j) = tau_j.
+// caller's GEMM router when given) as the inverse of diag(1/tau) + striu(S), one column per warp.
 #include <algorithm>
 
 #include "rrf_internal.cuh"
@@ -250,41 +249,38 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
   }
 }
 
-// Forward recurrence for the compact-WY factor from S = Y^T Y (one CTA; w <= 256):
-//   Tf(0:j, j) = -tau_j Tf(0:j, 0:j) S(0:j, j),  Tf(j, j) = tau_j.
-// For each column the 8 warps split the inner index l and the lanes cover the rows, so the FP64 chains
-// are j/8 long instead of j; partial sums are combined in warp order (deterministic).
-__global__ void __launch_bounds__(NT) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
-                                                   const double* __restrict__ tau, double* Tf, int64_t ldt) {
-  __shared__ double sc[kMaxW];
-  __shared__ double part[NT / 32][kMaxW];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = NT / 32;
-  for (int j = 0; j < w; ++j) {
-    for (int p = tid; p < j; p += NT) sc[p] = S[p + (int64_t)j * lds];
-    __syncthreads();
-    const int l0 = (j * warp) / NW, l1 = (j * (warp + 1)) / NW;
-    for (int p = lane; p < j; p += 32) {
-      double acc = 0.0;
-      for (int l = max(l0, p); l < l1; ++l) acc = fma(Tf[p + (int64_t)l * ldt], sc[l], acc);
-      part[warp][p] = acc;
-    }
-    __syncthreads();
-    const double tj = tau[j];
-    for (int p = tid; p < w; p += NT) {
-      double v = 0.0;
-      if (p < j) {
-        double acc = 0.0;
+// Compact-WY factor from S = Y^T Y and tau (Puglisi; Joffrain, Low, Quintana-Orti, van de Geijn and Van Zee,
+// "Accumulating Householder transformations, revisited", ACM TOMS 2006): with H_j = I - tau_j y_j y_j^T,
+// H_0 ... H_{w-1} = I - Y Tf Y^T where Tf^{-1} = diag(1/tau) + striu(S).  Reflectors with tau_j = 0 are the
+// identity and drop out: row and column j of Tf are zero, the rest is the inverse on the other indices.
+// Columns of the inverse are independent -- Tf(j, j) = tau_j, Tf(i, j) = -tau_i sum_{i<l<=j} S(i, l) Tf(l, j)
+// for i = j-1 .. 0 -- so each column is one warp's back substitution (lanes split the sum, fixed shuffle
+// tree: deterministic), and the w columns run on w / 8 CTAs at once instead of w dependent steps on one.
+constexpr int kLarftWarps = 8;
+__global__ void __launch_bounds__(32 * kLarftWarps) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
+                                                                 const double* __restrict__ tau, double* Tf,
+                                                                 int64_t ldt) {
+  __shared__ double tcol[kLarftWarps][kMaxW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * kLarftWarps + warp;
+  if (j >= w) return;
+  double* t = tcol[warp];
+  const double tj = tau[j];
+  if (lane == 0) t[j] = tj;
+  __syncwarp();
+  for (int i = j - 1; i >= 0; --i) {
+    const double ti = tau[i];
+    double dot = 0.0;
+    if (ti != 0.0 && tj != 0.0) {
+      const double* si = S + (int64_t)i * lds;  // S(l, i) = S(i, l): contiguous in l
+      for (int l = i + 1 + lane; l <= j; l += 32) dot = fma(si[l], t[l], dot);
 #pragma unroll
-        for (int q = 0; q < NW; ++q) acc += part[q][p];
-        v = -tj * acc;
-      } else if (p == j) {
-        v = tj;
-      }
-      Tf[p + (int64_t)j * ldt] = v;
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
     }
-    __syncthreads();
+    if (lane == 0) t[i] = (ti != 0.0 && tj != 0.0) ? -ti * dot : 0.0;
+    __syncwarp();
   }
+  for (int i = lane; i < w; i += 32) Tf[i + (int64_t)j * ldt] = (i <= j) ? t[i] : 0.0;
 }
 
 int choose_nb(int64_t r) {
@@ -311,7 +307,8 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
                      size_t scratch_bytes, WsHeader* hdr, cudaStream_t stream, const GemmEngine* eng) {
   if (w <= 0 || r <= 0) return cudaSuccess;
   if (w > kMaxW || r < w) return cudaErrorInvalidValue;
-  const int nb = choose_nb(r);
+  int nb = choose_nb(r);
+  if (eng != nullptr && eng->max_ctas > 0) nb = std::min(nb, eng->max_ctas);
   char* base = reinterpret_cast<char*>(scratch);
   size_t off = 0;
   double* partials = reinterpret_cast<double*>(base + off);
@@ -377,7 +374,8 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
     e = (eng != nullptr) ? gemm_run(*eng, &g, 1, stream)
                          : gemm_f64(&g, 1, reinterpret_cast<double*>(base + off), scratch_bytes - off, stream);
     if (e != cudaSuccess) return e;
-    larft_kernel<<<1, NT, 0, stream>>>((int)w, gram, w, tau, Tf, ldtf);
+    larft_kernel<<<(unsigned)((w + kLarftWarps - 1) / kLarftWarps), 32 * kLarftWarps, 0, stream>>>((int)w, gram, w, tau,
+                                                                                                Tf, ldtf);
     count_launch();
     e = cudaGetLastError();
   }

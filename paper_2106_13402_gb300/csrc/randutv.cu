@@ -48,6 +48,13 @@ struct RWs {
   double *Tq = nullptr, *Ry = nullptr, *Uy = nullptr, *Vy = nullptr, *sy = nullptr, *S1 = nullptr, *S2 = nullptr;
   // early termination: e_i^2 of the Frobenius recurrence (steps + 1) and the reduction's partial sums
   double *e2 = nullptr, *fpart = nullptr;
+  // b x b SVD beside the next step (see rrf_randutv): a second R / U_small / V_small / D set (the first is
+  // Rs / Us / Vs / sig, used by even steps), the side stream's own header and SVD scratch
+  double *Rs1 = nullptr, *Us1 = nullptr, *Vs1 = nullptr, *sig1 = nullptr;
+  double* Wkk = nullptr;  // b x b scratch of the explicit thin Q (never R, which the side stream may read)
+  WsHeader* hdr2 = nullptr;
+  double* jscr = nullptr;
+  size_t jscr_bytes = 0;
 };
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
@@ -80,6 +87,14 @@ size_t layout(int64_t m, int64_t n, int64_t b, int64_t p, bool bf16, int gemm_mo
   w.qdev = ar.take<int>(4);
   w.e2 = ar.take<double>(std::min((m + b - 1) / b, (n + b - 1) / b) + 1);
   w.fpart = reinterpret_cast<double*>(ar.take<char>(frob_scratch_bytes()));
+  w.Rs1 = ar.take<double>(b * b);
+  w.Us1 = ar.take<double>(b * b);
+  w.Vs1 = ar.take<double>(b * b);
+  w.sig1 = ar.take<double>(b);
+  w.Wkk = ar.take<double>(b * b);
+  w.hdr2 = reinterpret_cast<WsHeader*>(ar.take<char>(kHeaderBytes));
+  w.jscr_bytes = jacobi_scratch_bytes(std::min(b, n));
+  w.jscr = reinterpret_cast<double*>(ar.take<char>(std::max<size_t>(w.jscr_bytes, 256)));
   if (p > 0) {
     w.Qk = ar.take<double>(m * kb);
     w.Xk = ar.take<double>(m * b);
@@ -180,7 +195,7 @@ cudaError_t apply_t22(bool transposed, int64_t r, int64_t c, int64_t b, const do
 // Orthonormal basis (explicit thin Q, rows x b) of X via the panel Householder QR; X is overwritten.
 cudaError_t orthonormalize(int64_t rows, int64_t b, double* X, double* Qout, const RWs& w, cudaStream_t s) {
   cudaError_t e = panel_qr(rows, b, X, rows, w.tauu, w.Yu, rows, w.Tu, b, nullptr, 0, w.panel, w.panel_bytes, w.hdr, s, &w.eng);
-  if (e == cudaSuccess) e = explicit_q(rows, b, w.Yu, w.Tu, w.Rs, Qout, w, s);
+  if (e == cudaSuccess) e = explicit_q(rows, b, w.Yu, w.Tu, w.Wkk, Qout, w, s);
   return e;
 }
 
@@ -290,6 +305,35 @@ cudaError_t boosted_next(int64_t c, int64_t b, int64_t pk, const RWs& w, cudaStr
   if (e == cudaSuccess) e = copy_matrix(c - b, pk, Wr + b, c, w.Wn, c - b, s);
   return e;
 }
+
+// A second stream (per host thread and device, created once) on which the b x b SVD of step i runs while
+// the main stream applies U_i and samples step i + 1; events hand R over and the SVD back.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_j[2] = {nullptr, nullptr};
+  int dev = -1;
+  bool ok = false;
+};
+
+SideStream* side_stream() {
+  thread_local SideStream ss;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (ss.ok && ss.dev == dev) return &ss;
+  if (ss.dev != -1) return nullptr;  // created for another device: no side stream on this one
+  ss.dev = dev;
+  if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventCreateWithFlags(&ss.ev_r[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ss.ev_j[k], cudaEventDisableTiming) != cudaSuccess)
+      return nullptr;
+  ss.ok = true;
+  return &ss;
+}
+
+// SMs the main stream leaves free while an SVD runs beside it (the 2-CTA cluster and the one-CTA FP32
+// pre-pass, with room for the cluster to find two SMs of one GPC).
+constexpr int kSideReserve = 4;
 
 rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, double* U,
                       int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, const rrf_opts* opts) {
@@ -406,6 +450,57 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
   bool stop = false;
   int64_t done = start;
   int* fgate = &w.hdr->flags[8];  // set when the recurrence fell below its accuracy floor
+  // The b x b SVD of step i runs on a side stream while the main stream applies U_i and samples step i + 1
+  // (their data are disjoint from R's SVD); its small updates then run on the main stream just before
+  // V_{i+1} is applied -- the first operation that touches what they write (the row block T(I2, J3)) --
+  // so every element sees the same operations in the same order as in the serial schedule, and the result
+  // is the same bit for bit.  Not with the learned policy (its features wait for the SVD) or a Frobenius
+  // tolerance (the stop test waits for the small updates), nor for b > 128.
+  SideStream* side = (!learned && frob_tol == 0.0 && b <= 128) ? side_stream() : nullptr;
+  RRF_CUDA_TRY(cudaMemsetAsync(w.hdr2, 0, kHeaderBytes, s));
+  struct Pend {
+    bool on;
+    int64_t i, o, r, c;
+    int par;
+  } pend = {false, 0, 0, 0, 0, 0};
+  // U(:, I2) U_small, V(:, J2) V_small, U_small^T T(I2, J3), T(I1, J2) V_small, T(I2 u I3, J2) = [D; 0] of the
+  // pending step, then its Frobenius recurrence.
+  auto small_updates = [&]() -> cudaError_t {
+    const int64_t o = pend.o, r = pend.r, c = pend.c, nc = c - b;
+    const double* Usp = pend.par ? w.Us1 : w.Us;
+    const double* Vsp = pend.par ? w.Vs1 : w.Vs;
+    const double* sgp = pend.par ? w.sig1 : w.sig;
+    double* T22p = T + o + o * ldt;
+    double* UI2 = U + o * ldu;
+    double* VJ2 = V + o * ldv;
+    double* TI2J3 = T + o + (o + b) * ldt;
+    double* TI1J2 = T + o * ldt;
+    pend.on = false;
+    GemmDesc g[4] = {gd(m, b, b, UI2, ldu, 0, Usp, b, 0, w.Xa, m),
+                     gd(n, b, b, VJ2, ldv, 0, Vsp, b, 0, w.Xb, n),
+                     gd(b, nc, b, Usp, b, 1, TI2J3, ldt, 0, w.Wa, b),
+                     gd(o, b, b, TI1J2, ldt, 0, Vsp, b, 0, w.Xc, std::max<int64_t>(o, 1))};
+    cudaError_t e = gemm_run(w.eng, g, o > 0 ? 4 : 3, s);
+    if (e == cudaSuccess) e = copy_matrix(m, b, w.Xa, m, UI2, ldu, s);
+    if (e == cudaSuccess) e = copy_matrix(n, b, w.Xb, n, VJ2, ldv, s);
+    if (e == cudaSuccess) e = copy_matrix(b, nc, w.Wa, b, TI2J3, ldt, s);
+    if (e == cudaSuccess && o > 0) e = copy_matrix(o, b, w.Xc, o, TI1J2, ldt, s);
+    if (e == cudaSuccess) e = set_diag_block(r, b, sgp, T22p, ldt, s);
+    if (e == cudaSuccess && frob) {  // e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2; direct below the floor
+      e = frob_step(b, c, T22p, ldt, w.fpart, w.e2, pend.i, false, start, fgate, s);
+      if (e == cudaSuccess) e = frob_refresh(r - b, c - b, T22p + b + b * ldt, ldt, w.fpart, w.e2, pend.i, fgate, s);
+    }
+    return e;
+  };
+  auto flush = [&]() -> cudaError_t {
+    if (!pend.on) return cudaSuccess;
+    if (side != nullptr) {
+      cudaError_t e = cudaStreamWaitEvent(s, side->ev_j[pend.par], 0);
+      if (e != cudaSuccess) return e;
+      w.eng.max_ctas = 0;
+    }
+    return small_updates();
+  };
   if (frob) {  // e_start from its definition: ||A||_F, or the trailing block's norm when resuming
     const int64_t o = b * start;
     if (start == 0) RRF_CUDA_TRY(frob_step(m, n, A, lda, w.fpart, w.e2, 0, true, 0, fgate, s));
@@ -451,7 +546,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
             RRF_CUDA_TRY(cudaStreamSynchronize(s));
           }
           if (reorth && qi > 0) {  // the QR just computed gives the orthonormal start for free
-            RRF_CUDA_TRY(explicit_q(c, b, w.Yv, w.Tv, w.Rs, w.Qt, w, s));
+            RRF_CUDA_TRY(explicit_q(c, b, w.Yv, w.Tv, w.Wkk, w.Qt, w, s));
             start = w.Qt;
           }
         }
@@ -461,6 +556,8 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
       // V_i = I - Yv Tv Yv^T from HQR_full(Y); T(:, o:) and V(:, o:) <- (.) V_i.
       RRF_CUDA_TRY(panel_qr(c, b, w.Y, c, w.tauv, w.Yv, c, w.Tv, b, nullptr, 0, w.panel, w.panel_bytes,
                             w.hdr, s, &w.eng));
+      // The previous step's small updates go first: its row block T(I2, J3) meets this V_i next.
+      RRF_CUDA_TRY(flush());
       {
         double* CT = T + o * ldt;
         double* CV = V + o * ldv;
@@ -478,9 +575,22 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         RRF_CUDA_TRY(boosted_next(c, b, pk, w, s));
         have_next = pk > 0;
       }
-      // [U_i, R] = HQR_full(T(o:, o:o+b)).
-      RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, w.Rs, b, w.panel, w.panel_bytes,
+      // [U_i, R] = HQR_full(T(o:, o:o+b)); R goes to this step's parity buffer.
+      const int par = (int)(i & 1);
+      double* Rp = par ? w.Rs1 : w.Rs;
+      RRF_CUDA_TRY(panel_qr(r, b, T22, ldt, w.tauu, w.Yu, r, w.Tu, b, Rp, b, w.panel, w.panel_bytes,
                             w.hdr, s, &w.eng));
+      if (side != nullptr) {
+        // SVD of R on the side stream, beside U_i's application and the next step's sample; the main
+        // stream keeps kSideReserve SMs free for it until it waits for the result.
+        RRF_CUDA_TRY(cudaEventRecord(side->ev_r[par], s));
+        RRF_CUDA_TRY(cudaStreamWaitEvent(side->s, side->ev_r[par], 0));
+        RRF_CUDA_TRY(jacobi_svd(b, Rp, b, par ? w.Us1 : w.Us, b, par ? w.sig1 : w.sig, par ? w.Vs1 : w.Vs, b, w.hdr2,
+                                side->s, w.jscr, w.jscr_bytes, true));
+        RRF_CUDA_TRY(cudaEventRecord(side->ev_j[par], side->s));
+        w.eng.max_ctas = std::max(1, dev_info().sms - kSideReserve);
+        pend = {true, i, o, r, c, par};
+      }
       {
         double* C = T + o + (o + b) * ldt;  // r x (c - b)
         double* CU = U + o * ldu;           // m x r
@@ -495,32 +605,17 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
                           gd(m, r, b, w.Xc, m, 0, w.Yu, r, 1, CU, ldu, -1.0, 1.0)};
         RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
       }
-      // SVD of R and the small updates.
-      RRF_CUDA_TRY(jacobi_svd(b, w.Rs, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s, w.gemm, w.gemm_bytes));
-      {
-        const int64_t nc = c - b;
-        double* UI2 = U + o * ldu;
-        double* VJ2 = V + o * ldv;
-        double* TI2J3 = T + o + (o + b) * ldt;
-        double* TI1J2 = T + o * ldt;
-        GemmDesc g[4] = {gd(m, b, b, UI2, ldu, 0, w.Us, b, 0, w.Xa, m),
-                         gd(n, b, b, VJ2, ldv, 0, w.Vs, b, 0, w.Xb, n),
-                         gd(b, nc, b, w.Us, b, 1, TI2J3, ldt, 0, w.Wa, b),
-                         gd(o, b, b, TI1J2, ldt, 0, w.Vs, b, 0, w.Xc, std::max<int64_t>(o, 1))};
-        RRF_CUDA_TRY(gemm_run(w.eng, g, o > 0 ? 4 : 3, s));
-        RRF_CUDA_TRY(copy_matrix(m, b, w.Xa, m, UI2, ldu, s));
-        RRF_CUDA_TRY(copy_matrix(n, b, w.Xb, n, VJ2, ldv, s));
-        RRF_CUDA_TRY(copy_matrix(b, nc, w.Wa, b, TI2J3, ldt, s));
-        if (o > 0) RRF_CUDA_TRY(copy_matrix(o, b, w.Xc, o, TI1J2, ldt, s));
-        RRF_CUDA_TRY(set_diag_block(r, b, w.sig, T22, ldt, s));
-      }
-      if (frob) {  // e_i^2 = e_{i-1}^2 - ||T(I2, J2 u J3)||_F^2; summed directly below the recurrence's floor
-        RRF_CUDA_TRY(frob_step(b, c, T22, ldt, w.fpart, w.e2, i, false, start, fgate, s));
-        RRF_CUDA_TRY(frob_refresh(r - b, c - b, T22 + b + b * ldt, ldt, w.fpart, w.e2, i, fgate, s));
+      if (side == nullptr) {
+        // SVD of R and the small updates, in order.  The same (narrow) SVD kernel as on the side stream, so
+        // both schedules give the same bits.
+        RRF_CUDA_TRY(jacobi_svd(b, Rp, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s, w.gemm, w.gemm_bytes, true));
+        pend = {true, i, o, r, c, 0};
+        RRF_CUDA_TRY(small_updates());
         if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(i, &stop));
       }
     } else {
       // Final block: SVD of the r x c remainder (c <= b).
+      RRF_CUDA_TRY(flush());
       const double* M = T22;
       int64_t ldm = ldt;
       if (r > c) {
@@ -553,6 +648,8 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
     }
     done = i;
   }
+  RRF_CUDA_TRY(flush());
+  if (side != nullptr) RRF_CUDA_TRY(merge_status(&w.hdr->status, &w.hdr2->status, s));
   if (opts != nullptr && opts->steps_out != nullptr) *opts->steps_out = (int)done;
   if (opts != nullptr && opts->frob_out != nullptr) {
     std::vector<double> e2((size_t)done + 1);

@@ -106,7 +106,7 @@ bool ozaki_eligible(const GemmDesc& d, bool force);
 size_t ozaki_scratch_bytes(int64_t M, int64_t N, int64_t K);
 // d.M is the long side (>= 256); set out_transposed to write C^T (element (i, j) at C[j + i ldc]).
 cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, size_t scratch_bytes, int* status,
-                       cudaStream_t s);
+                       cudaStream_t s, int max_ctas = 0);
 
 // Where the drivers send FP64 GEMMs: the DFMA kernel, or the emulation for the large ones.
 struct GemmEngine {
@@ -117,6 +117,8 @@ struct GemmEngine {
   int* status = nullptr;
   bool emulate = false;
   bool force = false;  // emulate every eligible shape, not only large products
+  int max_ctas = 0;    // > 0: persistent and cooperative kernels use at most this many CTAs (SMs left free
+                       // for work on another stream)
 };
 // Bytes of emulation scratch that cover every GEMM of a factorization of an m x n matrix with panel b.
 size_t ozaki_bound(int64_t m, int64_t n, int64_t b);
@@ -141,9 +143,10 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
 // One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.  With scratch of at least
 // jacobi_scratch_bytes(c) (> 0 for 32 <= c <= 256) an FP32 pre-pass supplies the starting V.
 size_t jacobi_scratch_bytes(int64_t c);
+// narrow: use the fewest SMs (a 2-CTA cluster for c <= 128), for an SVD that runs beside other kernels.
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch = nullptr,
-                       size_t scratch_bytes = 0);
+                       size_t scratch_bytes = 0, bool narrow = false);
 
 // ---- BF16 tensor-core GEMM (gemm_bf16_tc.cu) ------------------------------------------------------
 // D (FP64, M x N, ldd) = alpha * A (M x K) B (N x K)^T, BF16 operands with K contiguous (ld multiple of 8,
@@ -188,6 +191,8 @@ cudaError_t frob_step(int64_t rows, int64_t cols, const double* X, int64_t ld, d
                       bool first, int64_t base, int* gate, cudaStream_t s);
 cudaError_t frob_refresh(int64_t rows, int64_t cols, const double* X, int64_t ld, double* part, double* e2,
                          int64_t idx, int* gate, cudaStream_t s);
+// *dst = *src if *dst is still 0 (the first recorded device condition wins)
+cudaError_t merge_status(int* dst, const int* src, cudaStream_t s);
 // status |= NUMERICAL if any entry of the block is not finite
 cudaError_t check_finite(int64_t rows, int64_t cols, const double* X, int64_t ld, int* status,
                          cudaStream_t s);
