@@ -64,8 +64,9 @@ def parse():
                    help="c2: FP64 randUTV + powerURV 8192^2 (default); c3: BF16-sketch randUTV 16384^2, b=256, q=2; "
                         "c4: 512 uneven FP32 powerURV in one graph; c5: learned q + BF16 sketch, 8192^2, b=128; "
                         "gemm: the dominant kernel alone (FP64 GEMM 4096^3 emulated on the tensor cores); "
-                        "boosted: randUTV_boosted 8192^2, b=128, q=2, p=--oversample")
+                        "boosted: randUTV_boosted 8192^2, b=128, q=--boost-q, p=--oversample")
     p.add_argument("--oversample", type=int, default=128, help="p of the boosted workload")
+    p.add_argument("--boost-q", type=int, default=5, help="q of the boosted workload")
     return p.parse_args()
 
 
@@ -256,6 +257,7 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
     """Read the GEMM event profiler (after rrf_gemm_profile_end) and describe the dominant kernel."""
     gemm_ms, gemm_flops, gemm_launches = rrf.gemm_profile_end()
     emu_ms, emu_flops, emu_tflops, emu_launches = rrf.gemm_profile_emulated()
+    emu_bytes = rrf.gemm_profile_emulated_bytes()
     if emu_ms > gemm_ms:
         # the emulated GEMM's tensor-core kernel (BF16 digit products, timed inside a long step -> the
         # sustained BF16 peak)
@@ -266,6 +268,8 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
                 "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "traffic_source": tsrc,
                 "traffic_unit": "DRAM bytes read + written per launch, averaged over the launches of one step",
+                "algorithmic_bytes_per_launch": round(emu_bytes / max(emu_launches, 1)),
+                "achieved_gbs_algorithmic": round(emu_bytes / (emu_ms / 1e3) / 1e9, 1),
                 "peak_source": f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
                 "work": "28 digit-pair products x 2 M N K' BF16 flops per launch (K' = K rounded up to 32)",
                 "fp64_equivalent_tflops": round(emu_flops / (emu_ms / 1e3) / 1e12, 3),
@@ -284,7 +288,7 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
 def extras_8192(torch, rrf, testmats, A, s, dev, n, b):
     """Sub-results for the configurations the speed-up target is set on, on the same 8192^2 matrix:
     (1) learned per-step q with the BF16 sketch (fallback q = 2) against the plain FP64 method with q = 2;
-    (2) randUTV_boosted (Algorithm 2, q = 2, p = b) against the same algorithm with every product on the
+    (2) randUTV_boosted (Algorithm 2, q = 5, p = b) against the same algorithm with every product on the
     DFMA pipe.  One warm run and one timed run each; e_k / sigma_{k+1} at every block boundary."""
     from paper_2106_13402_gb300 import qpolicy
     ks = list(range(b, n, b))
@@ -293,10 +297,10 @@ def extras_8192(torch, rrf, testmats, A, s, dev, n, b):
     stream = torch.cuda.current_stream()
     on_target = lambda r: sum(1 for v in r.values() if v <= 1.1)
 
-    def timed(opts):
+    def timed(opts, q=2):
         ws = rrf.workspace(rrf.randutv_workspace_bytes(n, n, b, opts), dev)
-        rrf.randutv(A, b, 2, 17, opts=opts, ws=ws, out=out)
-        t = _event_ms(torch, lambda: rrf.randutv(A, b, 2, 17, opts=opts, ws=ws, out=out, check_status=False), stream)
+        rrf.randutv(A, b, q, 17, opts=opts, ws=ws, out=out)
+        t = _event_ms(torch, lambda: rrf.randutv(A, b, q, 17, opts=opts, ws=ws, out=out, check_status=False), stream)
         st = rrf.lib().rrf_workspace_status(rrf._vp(ws.data_ptr()), rrf._stream(None))
         r = _boundary_ratios(torch, out[1], s, b, ks)
         del ws
@@ -315,11 +319,14 @@ def extras_8192(torch, rrf, testmats, A, s, dev, n, b):
             "max_ratio": max(r_fast.values()), "plain_max_ratio": max(r_plain.values()),
             "q_used": {"mean": round(sum(qs) / len(qs), 3), "hist": [qs.count(v) for v in range(4)]},
             "device_status": st}
-    bms, r_boost, st = timed(rrf.make_opts(oversample=b))
-    bpms, r_bplain, _ = timed(rrf.make_opts(oversample=b, gemm_mode=rrf.GEMM_NATIVE))
-    res["boosted_q2_p128"] = {
+    # randUTV_boosted with q = 5, p = b: the oracle meets e_k <= 1.1 sigma_{k+1} at every block boundary of
+    # this spectrum's shape with it (2048^2 proxy with the same decay per block), q = 2 at 57 of 63
+    qb = 5
+    bms, r_boost, st = timed(rrf.make_opts(oversample=b), q=qb)
+    bpms, r_bplain, _ = timed(rrf.make_opts(oversample=b, gemm_mode=rrf.GEMM_NATIVE), q=qb)
+    res["boosted_q5_p128"] = {
         "ms": round(bms, 1), "speedup_vs_plain_fp64_boosted": round(bpms / bms, 3), "plain_fp64_boosted_ms": round(bpms, 1),
-        "speedup_vs_plain_fp64_basic_q2": round(pms / bms, 3),
+        "speedup_vs_plain_fp64_basic_q2": round(pms / bms, 3), "plain_fp64_boosted_on_target": on_target(r_bplain),
         "on_target": on_target(r_boost), "boundaries": len(ks), "max_ratio": max(r_boost.values()),
         "device_status": st}
     return res
@@ -699,13 +706,13 @@ def run_c3_c5(args):
 
 
 def run_boosted(args):
-    """randUTV_boosted (Algorithm 2) on the 8192^2 spectrum: 8192^2, b = 128, q = 2, p = --oversample (default
-    b), the paper's remedy for e_k above 1.1 sigma_{k+1} at block boundaries.  Timed against randUTV_basic with
+    """randUTV_boosted (Algorithm 2) on the 8192^2 spectrum: 8192^2, b = 128, q = --boost-q (default 5),
+    p = --oversample (default b), the paper's remedy for e_k above 1.1 sigma_{k+1} at block boundaries.  Timed against randUTV_basic with
     the same q and routing and against the plain FP64 method (DFMA products) of the same boosted algorithm;
     e_k / sigma_{k+1} at every block boundary for each."""
     torch, dev = _setup_single_gpu(args)
     from paper_2106_13402_gb300 import rrf, testmats
-    n, b, q, p = 8192, 128, 2, args.oversample
+    n, b, q, p = 8192, 128, args.boost_q, args.oversample
     A, s = testmats.make_matrix(n, n, "c2", 11, 12, device=str(dev))
     fast = rrf.make_opts(oversample=p)
     basic = rrf.make_opts()
@@ -747,7 +754,7 @@ def run_boosted(args):
     ach = emu_tflops / (emu_ms / 1e3) / 1e12 if emu_ms > 0 else 0.0
     on_target = lambda r: sum(1 for v in r.values() if v <= 1.1)
     line = {
-        "metric": f"factorizations/s (randUTV_boosted, 8192^2, b=128, q=2, p={p}) vs plain FP64",
+        "metric": f"factorizations/s (randUTV_boosted, 8192^2, b=128, q={q}, p={p}) vs plain FP64",
         "value": round(1e3 / ms, 5), "unit": "factorizations/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -175,9 +175,9 @@ struct GemmProfile {
   bool on = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> kind;
-  std::vector<double> flops, tflops;
+  std::vector<double> flops, tflops, bytes;
   size_t used = 0;
-  double ms_k[kKinds] = {}, flops_k[kKinds] = {}, tflops_k[kKinds] = {};
+  double ms_k[kKinds] = {}, flops_k[kKinds] = {}, tflops_k[kKinds] = {}, bytes_k[kKinds] = {};
   int64_t launches_k[kKinds] = {};
 };
 GemmProfile& prof() {
@@ -187,7 +187,7 @@ GemmProfile& prof() {
 
 }  // namespace
 
-cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream) {
+cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream, double bytes) {
   GemmProfile& pf = prof();
   if (!pf.on) return nullptr;
   std::lock_guard<std::mutex> lock(pf.mu);
@@ -197,6 +197,7 @@ cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cu
   pf.kind[r] = kind;
   pf.flops[r] = flops;
   pf.tflops[r] = tensor_flops;
+  pf.bytes[r] = bytes;
   cudaEvent_t end = pf.ev[pf.used + 1];
   pf.used += 2;
   return end;
@@ -286,9 +287,10 @@ extern "C" int rrf_gemm_profile_begin(int max_launches) {
   pf.kind.assign(pf.ev.size() / 2, 0);
   pf.flops.assign(pf.ev.size() / 2, 0.0);
   pf.tflops.assign(pf.ev.size() / 2, 0.0);
+  pf.bytes.assign(pf.ev.size() / 2, 0.0);
   pf.used = 0;
   for (int k = 0; k < rrf::kKinds; ++k) {
-    pf.ms_k[k] = pf.flops_k[k] = pf.tflops_k[k] = 0.0;
+    pf.ms_k[k] = pf.flops_k[k] = pf.tflops_k[k] = pf.bytes_k[k] = 0.0;
     pf.launches_k[k] = 0;
   }
   pf.on = true;
@@ -309,6 +311,7 @@ extern "C" int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches
       pf.ms_k[k] += t;
       pf.flops_k[k] += pf.flops[i / 2];
       pf.tflops_k[k] += pf.tflops[i / 2];
+      pf.bytes_k[k] += pf.bytes[i / 2];
       pf.launches_k[k] += 1;
     }
   }
@@ -337,5 +340,13 @@ extern "C" int rrf_gemm_profile_emulated(double* ms, double* flops, double* tens
   if (flops) *flops = pf.flops_k[1];
   if (tensor_flops) *tensor_flops = pf.tflops_k[1];
   if (launches) *launches = pf.launches_k[1];
+  return 0;
+}
+
+extern "C" int rrf_gemm_profile_emulated_bytes(double* bytes) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  if (pf.on) return 1;
+  if (bytes) *bytes = pf.bytes_k[1];
   return 0;
 }

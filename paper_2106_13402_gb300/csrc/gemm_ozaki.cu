@@ -65,6 +65,7 @@ struct OzParams {
   int ct;               // write C^T: element (row, col) at C[col + row ldc]
   int* status;
   int amode;            // alpha: 1 -> +1, 2 -> -1, 0 -> any other value
+  int bmode;            // beta != 0 (decided on the host: no FP64 comparison in the kernel)
   long long stall_cycles;  // failure injection only (0 normally): the MMA warp first waits this long on a
                            // barrier nothing arrives on, then aborts
 };
@@ -155,6 +156,20 @@ __device__ __forceinline__ int exact_int(uint32_t bits) {
   return __float_as_int(__fadd_rn(__uint_as_float(bits), kMagic)) - kMagicBits;
 }
 
+// Exact integer value of an integer-valued FP32 word with |x| < 2^24, with integer instructions only (a
+// conversion instruction would run on the FP64 pipe): x = m 2^(e - 150) with the implicit bit in m.
+__device__ __forceinline__ int exact_int_wide(uint32_t bits) {
+  const int e = (int)((bits >> 23) & 0xFFu);  // 0 only for x = 0; 127..150 for 1 <= |x| < 2^24
+  const int m = (int)((bits & 0x7FFFFFu) | 0x800000u);
+  const int v = (e >= 127) ? (m >> (150 - e)) : 0;
+  return (bits >> 31) ? -v : v;
+}
+
+// The rare exponents (subnormal or overflowing results) take the FP64 path, kept out of line so that the
+// compiler does not predicate its FP64 instructions into every output.
+__device__ __noinline__ double scaled_fp64(long long W, int x) { return ldexp((double)W, x); }
+__device__ __noinline__ double times_alpha(double alpha, double v) { return alpha * v; }
+
 // (acc + ta) 2^x as an FP64 value, for an exact integer acc and a fraction |ta| <= 1/2, with integer
 // instructions only: this GPU's FP64 pipe does ~2 operations per clock per SM, far too few for a
 // conversion, an add and a scaling per output.  The fixed-point value W = acc 2^10 + round(ta 2^10) (acc
@@ -181,7 +196,7 @@ __device__ __forceinline__ double fixed_to_double(long long acc, float ta, int x
     m >>= 1;
     ++e;
   }
-  if (e < -1022 || e > 1023) return ldexp((double)W, xs);
+  if (e < -1022 || e > 1023) return scaled_fp64(W, xs);
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
@@ -321,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // Epilogue warps ew = 0..15: TMEM lane quadrant (warp % 4) = 32 tile rows, columns 8 (ew / 4) .. +7.
+    const bool beta_nz = p.bmode != 0;
     const int ew = warp - 2;
     const int quad = warp & 3;
     const int col0 = (ew >> 2) * 8;
@@ -358,10 +374,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           // Over a round of 64 of K, |S_d| <= (d + 1) 64 2^14: S_0 .. S_3 are within 2^22 and convert exactly
-          // by the magic-number add; S_4 (up to 5 2^20) by a round-to-nearest conversion instruction.
+          // by the magic-number add; S_4 (up to 5 2^20) from its bit pattern.
           const int hi = exact_int(v[0][c]) * 256 + exact_int(v[1][c]);   // |.| < 2^29
           const int mid = exact_int(v[2][c]) * 256 + exact_int(v[3][c]);  // |.| < 2^30
-          const int d4 = __float2int_rn(__uint_as_float(v[4][c]));
+          const int d4 = exact_int_wide(v[4][c]);
           float t = fmaf(__uint_as_float(v[5][c]), 0.00390625f, ta[c]);
           t = fmaf(__uint_as_float(v[6][c]), 1.52587890625e-05f, t);
           const float r = __fadd_rn(t, kMagic);
@@ -374,18 +390,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = m0 + quad * 32 + lane;
       if (row >= p.M) continue;
       const int er = p.ea[row];
+      // All loads of the tile's outputs first (column exponents, and C when beta != 0), so their latencies
+      // overlap instead of each waiting behind the previous column's store.
+      int ec[8];
+      double cin[8];
+      const bool direct = p.splits == 1;
+      const bool has_beta = beta_nz;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t col = n0 + col0 + c;
+        ec[c] = col < p.N ? p.eb[col] : 0;
+        cin[c] = 0.0;
+        if (direct && has_beta && col < p.N) cin[c] = p.ct ? p.C[col + row * p.ldc] : p.C[row + col * p.ldc];
+      }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t col = n0 + col0 + c;
         if (col >= p.N) continue;
         // value = 2^(e_r + f_c) sum_d S_d 2^-8(d+2) = (acc + ta) 2^(e_r + f_c - 48), assembled with integer
         // instructions; alpha = +-1 is a sign change, other alpha one FP64 multiply, beta != 0 one FP64 FMA.
-        double v = nch > 0 ? fixed_to_double(acc[c], ta[c], er + p.eb[col] - 48) : 0.0;
-        if (p.splits == 1) {
+        double v = nch > 0 ? fixed_to_double(acc[c], ta[c], er + ec[c] - 48) : 0.0;
+        if (direct) {
           double* cp = p.ct ? p.C + col + row * p.ldc : p.C + row + col * p.ldc;
           if (p.amode == 2) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
-          else if (p.amode == 0) v = p.alpha * v;
-          if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+          else if (p.amode == 0) v = times_alpha(p.alpha, v);
+          if (has_beta) v = fma(p.beta, cin[c], v);
           *cp = v;
         } else {
           p.C[((int64_t)split * p.N + col) * p.M + row] = v;
@@ -414,6 +443,13 @@ __device__ __forceinline__ int scale_exponent(unsigned long long m) {
   const int E = (int)(m >> 52);
   if (E != 0) return E - 1021;
   return (64 - __clzll((long long)m)) - 1074 + 1;  // subnormal: m * 2^-1074
+}
+
+// BF16 of an integer |d| <= 128 (exact: at most 8 significant bits) without a conversion instruction (those
+// run on the FP64 pipe): the magic-number add gives the FP32 value, whose upper half is the BF16 pattern.
+__device__ __forceinline__ __nv_bfloat16 small_int_bf16(int d) {
+  const float f = __fsub_rn(__int_as_float(kMagicBits + d), kMagic);
+  return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
 }
 
 // Row maxima (as bit patterns with the sign cleared) of X(r, k) = X[r sr + k sk]; mx must be zeroed first.
@@ -492,9 +528,9 @@ __global__ void oz_split_kernel(int64_t rows, int64_t K, int64_t Kp, const doubl
       const int sb = 8 * (kS - 1 - sl);
       const long long dg = (Xi + (1ll << (sb - 1))) >> sb;
       Xi -= dg << sb;
-      D[((int64_t)sl * rows + r) * Kp + k] = __float2bfloat16_rn((float)dg);
+      D[((int64_t)sl * rows + r) * Kp + k] = small_int_bf16((int)dg);
     }
-    D[((int64_t)(kS - 1) * rows + r) * Kp + k] = __float2bfloat16_rn((float)Xi);
+    D[((int64_t)(kS - 1) * rows + r) * Kp + k] = small_int_bf16((int)Xi);
   }
 }
 
@@ -661,6 +697,7 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   p.ea = ea; p.eb = eb;
   p.alpha = d.alpha; p.beta = d.beta;
   p.amode = d.alpha == 1.0 ? 1 : (d.alpha == -1.0 ? 2 : 0);
+  p.bmode = d.beta != 0.0 ? 1 : 0;
   p.C = splits == 1 ? d.C : part;
   p.ldc = d.ldc;
   p.ct = out_transposed ? 1 : 0;
@@ -669,7 +706,10 @@ cudaError_t gemm_ozaki(const GemmDesc& d, bool out_transposed, char* scratch, si
   p.stall_cycles = inj.kind == RRF_INJECT_GEMM_STALL ? inj.value : 0;
   const unsigned grid = (unsigned)std::min<int64_t>(p.units, max_ctas > 0 ? std::min(max_ctas, sms) : sms);
   // profiled work: the FP64 product's 2 M N K, and the tensor work 28 x 2 M N Kp of the digit products
-  cudaEvent_t ev_end = profile_launch_begin(1, 2.0 * M * N * K, 56.0 * M * N * Kp, s);
+  // algorithmic bytes: the 7 BF16 digit slices of op(A) and op(B) read once, C written once (read once more
+  // when beta != 0; split partials instead when K is split)
+  const double abytes = 14.0 * (double)(M + N) * Kp + 8.0 * M * N * (splits > 1 ? splits : (d.beta != 0.0 ? 2 : 1));
+  cudaEvent_t ev_end = profile_launch_begin(1, 2.0 * M * N * K, 56.0 * M * N * Kp, s, abytes);
   ozaki_gemm_kernel<<<grid, kThreads, oz_smem(), s>>>(ma, mb, p);
   count_launch();
   if (ev_end != nullptr) cudaEventRecord(ev_end, s);

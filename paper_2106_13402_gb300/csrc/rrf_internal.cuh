@@ -99,7 +99,8 @@ cudaError_t gemm_f64(const GemmDesc* d, int count, double* scratch, size_t scrat
 // While GEMM profiling is on: record a start event on `stream` and return the end event to record after
 // the launch (null when profiling is off or its event pool is used up).  kind 0 = DFMA GEMM, 1 = emulated,
 // 2 = BF16 sketch GEMM (its third argument then carries algorithmic bytes).
-cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream);
+// `bytes`: the launch's algorithmic DRAM bytes (recorded for the emulated GEMM's tensor-core kernel).
+cudaEvent_t profile_launch_begin(int kind, double flops, double tensor_flops, cudaStream_t stream, double bytes = 0.0);
 
 // ---- FP64 GEMM emulated on the BF16 tensor cores (gemm_ozaki.cu) -------------------------------------
 bool ozaki_eligible(const GemmDesc& d, bool force);
