@@ -109,6 +109,38 @@ def make_matrix(m: int, n: int, profile: str, seed1: int, seed2: int, rank: int 
     return A, s
 
 
+POLICY_DECAY_CLASSES = ("exp", "poly", "sshape", "step")
+
+
+def policy_spectrum(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Training and held-out spectra of the learned q policy: one of four decay classes with random rates
+    (exponential, polynomial, S-shaped, step), drawn from `rng`."""
+    j = np.arange(n, dtype=np.float64)
+    cls = POLICY_DECAY_CLASSES[rng.integers(len(POLICY_DECAY_CLASSES))]
+    if cls == "exp":
+        s = np.exp(-rng.uniform(2.0, 40.0) * j / n)
+    elif cls == "poly":
+        s = (1.0 + j) ** (-rng.uniform(0.3, 3.0))
+    elif cls == "sshape":
+        c, w, lo = rng.uniform(0.05, 0.7) * n, rng.uniform(0.005, 0.1) * n, 10.0 ** rng.uniform(-5, -1)
+        s = lo + (1.0 - lo) / (1.0 + np.exp((j - c) / w))
+    else:
+        k, lo = int(rng.uniform(0.05, 0.8) * n), 10.0 ** rng.uniform(-6, -1)
+        s = np.where(j < k, 1.0, lo)
+    return np.sort(s)[::-1].copy()
+
+
+def policy_matrix(n: int, seed: int):
+    """(A, s): an n x n training matrix of the learned q policy, A = Q1 diag(s) Q2^T with s from
+    policy_spectrum(numpy PCG64(seed)) and Haar Q1, Q2 from numpy seeds 2 seed + 1, 2 seed + 2
+    (Fortran-ordered float64; the same on every machine)."""
+    rng = np.random.default_rng(seed)
+    s = policy_spectrum(n, rng)
+    q1 = _haar_np(n, n, 2 * seed + 1)
+    q2 = _haar_np(n, n, 2 * seed + 2)
+    return np.asfortranarray((q1 * s) @ q2.T), s
+
+
 def batch_shapes(count: int, seed: int, m_lo: int = 256, m_hi: int = 2048, n_lo: int = 128):
     """Uneven batch shapes: m ~ U[m_lo, m_hi], n ~ U[n_lo, m] (uniform integers), seeded."""
     rng = np.random.default_rng(seed)

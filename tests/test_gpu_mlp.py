@@ -125,7 +125,8 @@ def _policy_vs_fixed(params, count=8, n=1024, b=128, with_q3=False):
 def test_trained_policy_gains_over_fixed_q2():
     """The packaged network (trained on matrices the method factored itself) against the fallback q = 2 on
     held-out matrices of mixed decay: fewer power iterations in total, at least as many block boundaries
-    meeting the quality target e_k <= 1.1 sigma_{k+1}, and no boundary more than 3x the fallback's e_k."""
+    meeting the quality target e_k <= 1.1 sigma_{k+1}, and no boundary more than 25 % above the fallback's
+    e_k."""
     params = qpolicy.load()
     if params is None:
         pytest.skip("no trained policy packaged")
@@ -139,4 +140,4 @@ def test_trained_policy_gains_over_fixed_q2():
           f"of {len(rows)}; worst e_k learned / fixed {worst:.3f}")
     assert q_learned < q_fixed
     assert hit_l >= hit_f
-    assert worst <= 3.0
+    assert worst <= 1.25

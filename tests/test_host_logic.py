@@ -26,6 +26,15 @@ def test_acceptable_meets_target_or_stays_near_the_better_fallback():
     assert list(labels) == [0, 3, 3]
 
 
+def test_acceptable_requires_the_target_wherever_the_fallback_meets_it():
+    """q = 1 within 5 % of q = 2 is not enough when q = 2 meets 1.1 sigma_{k+1} and q = 1 does not."""
+    sig = np.array([1.0])
+    errs = np.array([[1.30], [1.12], [1.08], [1.07]])
+    ok = qpolicy.acceptable(errs, sig)[:, 0]
+    assert list(ok) == [False, False, True, True]
+    assert np.argmax(ok) == 2
+
+
 def test_acceptable_uses_the_better_of_q2_and_q3_as_reference():
     sig = np.array([0.5])
     errs = np.array([[1.0], [0.80], [0.70], [0.69]])
