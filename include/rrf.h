@@ -336,6 +336,9 @@ RRF_API rrf_status rrf_workspace_status(void* workspace, void* stream);
  * rrf_gemm_profile_emulated_bytes (after rrf_gemm_profile_end): the algorithmic DRAM bytes of those same
  *   launches: 14 (M + N) K' for the digit slices of op(A) and op(B), read once, plus 8 M N for C written
  *   once (twice when beta != 0: C is read too; splits x 8 M N of partial sums when K is split).
+ * rrf_gemm_profile_panel (after rrf_gemm_profile_end): the same for the Householder panel kernel of every
+ *   panel factorization (its compact-WY factor not included): device time, flops 2 r w^2 - 2 w^3 / 3,
+ *   algorithmic bytes 24 r w (the panel read and written back, the reflectors written) and launches.
  * rrf_gemm_profile_bf16 (after rrf_gemm_profile_end): the same for the tensor-core kernel of the BF16
  *   sketch GEMM (its split-K reduction not included): device time, flops 2 M N K, algorithmic bytes
  *   2 (M + N) K (BF16 operands read once) + 4 M N (one FP32 result per output) and launches.
@@ -346,6 +349,7 @@ RRF_API int rrf_gemm_profile_end(double* ms, double* flops, int64_t* launches);
 RRF_API int rrf_gemm_profile_emulated(double* ms, double* flops, double* tensor_flops, int64_t* launches);
 RRF_API int rrf_gemm_profile_bf16(double* ms, double* flops, double* bytes, int64_t* launches);
 RRF_API int rrf_gemm_profile_emulated_bytes(double* bytes);
+RRF_API int rrf_gemm_profile_panel(double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* ------------------------------------------------------------------------------------------------
  * Failure injection for tests (not part of the method; no counterpart in the paper).  Drives the

@@ -168,8 +168,9 @@ int plan_splits(const GemmDesc& d, int sms) {
 
 // Optional instrumentation: CUDA events around each launch (diagnostics API of rrf.h).
 // Event pairs around GEMM launches while profiling is on; kind 0 = DFMA GEMM (kernel + split-K reduce),
-// kind 1 = the emulated GEMM's tensor-core kernel, kind 2 = the BF16 sketch GEMM's tensor-core kernel.
-constexpr int kKinds = 3;
+// kind 1 = the emulated GEMM's tensor-core kernel, kind 2 = the BF16 sketch GEMM's tensor-core kernel,
+// kind 3 = the Householder panel kernel.
+constexpr int kKinds = 4;
 struct GemmProfile {
   std::mutex mu;
   bool on = false;
@@ -348,5 +349,16 @@ extern "C" int rrf_gemm_profile_emulated_bytes(double* bytes) {
   std::lock_guard<std::mutex> lock(pf.mu);
   if (pf.on) return 1;
   if (bytes) *bytes = pf.bytes_k[1];
+  return 0;
+}
+
+extern "C" int rrf_gemm_profile_panel(double* ms, double* flops, double* bytes, int64_t* launches) {
+  rrf::GemmProfile& pf = rrf::prof();
+  std::lock_guard<std::mutex> lock(pf.mu);
+  if (pf.on) return 1;
+  if (ms) *ms = pf.ms_k[3];
+  if (flops) *flops = pf.flops_k[3];
+  if (bytes) *bytes = pf.bytes_k[3];
+  if (launches) *launches = pf.launches_k[3];
   return 0;
 }

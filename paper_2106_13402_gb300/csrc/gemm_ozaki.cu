@@ -353,6 +353,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       float ta[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) { acc[c] = 0; ta[c] = 0.f; }
+      // The tile's column exponents and (beta != 0) C values are loaded before the first harvest, so their
+      // latency runs under the unit's MMAs; nothing else in this kernel writes this tile's C.
+      const int64_t row = m0 + quad * 32 + lane;
+      const bool direct = p.splits == 1;
+      int ec[8];
+      double cin[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t col = n0 + col0 + c;
+        ec[c] = col < p.N ? p.eb[col] : 0;
+        cin[c] = 0.0;
+        if (direct && beta_nz && row < p.M && col < p.N) cin[c] = p.ct ? p.C[col + row * p.ldc] : p.C[row + col * p.ldc];
+      }
       bool ok = true;
       for (int c0 = 0; c0 < nch; c0 += kHarvest, ++h) {
         const int bf = (int)(h & 1);
@@ -387,22 +400,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok || *(volatile int*)&abort_flag) break;
-      const int64_t row = m0 + quad * 32 + lane;
       if (row >= p.M) continue;
       const int er = p.ea[row];
-      // All loads of the tile's outputs first (column exponents, and C when beta != 0), so their latencies
-      // overlap instead of each waiting behind the previous column's store.
-      int ec[8];
-      double cin[8];
-      const bool direct = p.splits == 1;
       const bool has_beta = beta_nz;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int64_t col = n0 + col0 + c;
-        ec[c] = col < p.N ? p.eb[col] : 0;
-        cin[c] = 0.0;
-        if (direct && has_beta && col < p.N) cin[c] = p.ct ? p.C[col + row * p.ldc] : p.C[row + col * p.ldc];
-      }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t col = n0 + col0 + c;

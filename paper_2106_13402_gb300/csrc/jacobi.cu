@@ -486,9 +486,6 @@ size_t jacobi_smem(int c, int cl, bool pre) {
   return b + 2 * kMaxC * sizeof(double) + kMaxC * sizeof(int);
 }
 
-// Largest c a cluster of CL CTAs takes: two CTAs hold c <= 128 (rows of M and V in ~150 KB each).
-constexpr int max_c_for(int CL) { return CL >= 8 ? kMaxC : 128; }
-
 template <int CL, bool PRE>
 cudaError_t set_jacobi_attrs() {
   if (CL > 8) {
@@ -496,7 +493,7 @@ cudaError_t set_jacobi_attrs() {
     if (e != cudaSuccess) return e;
   }
   return cudaFuncSetAttribute(jacobi_kernel<CL, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)jacobi_smem(max_c_for(CL), CL, PRE));
+                              (int)jacobi_smem(kMaxC, CL, PRE));
 }
 
 // 16-CTA clusters are not portable: use them when the device accepts the attribute and can schedule one.
@@ -561,14 +558,15 @@ size_t jacobi_scratch_bytes(int64_t c) {
 
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch,
-                       size_t scratch_bytes, bool narrow) {
+                       size_t scratch_bytes) {
   if (c <= 0) return cudaSuccess;
   if (c > kMaxC) return cudaErrorInvalidValue;
   JacobiArgs a;
   a.c = (int)c;
-  // 16 CTAs only pay off when each holds enough rows (c > 128); measured on GB300.  `narrow` asks for the
-  // fewest SMs (2 for c <= 128), for an SVD that runs beside other work.
-  const int cl = (c > 128) ? jacobi_cluster_size() : (narrow ? 2 : 8);
+  // 16 CTAs only pay off when each holds enough rows (c > 128); measured on GB300.  For c <= 128 an
+  // 8-CTA cluster beats 2 or 4 CTAs even beside the trailing-update GEMMs (8192^2 randUTV, b = 128:
+  // 675 ms with 8, 697 ms with 4, 781 ms with 2).
+  const int cl = (c > 128) ? jacobi_cluster_size() : 8;
   a.rp = (int)((c + cl - 1) / cl);
   a.M = M;
   a.ldm = ldm;
@@ -647,8 +645,10 @@ cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int6
   }
   e = cudaMemsetAsync(&hdr->flags[0], 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  e = (cl == 16) ? launch_jacobi<16, false>(a, (int)c, stream)
-                  : (cl == 2 ? launch_jacobi<2, false>(a, (int)c, stream) : launch_jacobi<8, false>(a, (int)c, stream));
+  switch (cl) {
+    case 16: e = launch_jacobi<16, false>(a, (int)c, stream); break;
+    default: e = launch_jacobi<8, false>(a, (int)c, stream); break;
+  }
   count_launch();
   if (e != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

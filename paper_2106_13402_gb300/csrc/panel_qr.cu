@@ -23,6 +23,8 @@ namespace {
 constexpr int NT = 256;
 constexpr int kMaxW = 256;
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kMaxCtas = 160;                       // panel CTAs (one per SM at most)
+constexpr int kMaxLoads = kMaxCtas / 8;             // partial sums one thread adds per slot
 
 struct PanelArgs {
   int64_t r;
@@ -46,31 +48,33 @@ struct PanelArgs {
 
 // Bounded grid barrier over nblocks participants, each wait limited to wait_cycles.  Returns false (and
 // records RRF_TIMEOUT) if the wait gave up.
+// The arrival is an acquire-release at GPU scope (after the CTA barrier it covers the whole CTA's writes),
+// the wait an acquire, so no full fence is needed on either side.
 __device__ bool grid_sync(WsHeader* hdr, unsigned nblocks, long long wait_cycles, unsigned& gen, int* s_fail) {
   __syncthreads();
   if (threadIdx.x == 0) {
     *s_fail = 0;
     const unsigned target = gen + 1;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&hdr->bar_count, 1u);
+    unsigned arrived;
+    // acq_rel: the last arrival also acquires every earlier arrival's writes (it reads them next)
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&hdr->bar_count) : "memory");
     if (arrived == nblocks - 1) {
-      atomicExch(&hdr->bar_count, 0u);
-      __threadfence();
-      atomicExch(&hdr->bar_gen, target);
+      atomicExch(&hdr->bar_count, 0u);  // ordered before the release below; read only after it
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&hdr->bar_gen), "r"(target) : "memory");
     } else {
       const long long t0 = clock64();
-      volatile unsigned* g = &hdr->bar_gen;
-      while (*g != target) {
+      unsigned g;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&hdr->bar_gen) : "memory");
+        if (g == target) break;
         if (clock64() - t0 > wait_cycles) {
           set_status(&hdr->status, RRF_TIMEOUT);
           *s_fail = 1;
           break;
         }
-        __nanosleep(20);
       }
     }
     gen = target;
-    __threadfence();
     if (*(volatile int*)&hdr->status == RRF_TIMEOUT) *s_fail = 1;
   }
   __syncthreads();
@@ -129,6 +133,79 @@ __device__ void column_partials(const PanelArgs& a, int j, const double* Pl, int
   __syncthreads();
 }
 
+// Trailing update by reflector j (P(i, k) -= z_k v_i for i >= j, k > j; z pre-multiplied by tau) fused
+// with the partial sums of column j + 1 (those of column_partials(j + 1)): column j + 1 is updated first
+// and copied to xs, then one pass over the other columns updates each element and accumulates its product
+// with xs -- one read of the local panel and one CTA barrier fewer than updating and summing apart.
+__device__ void update_and_partials(const PanelArgs& a, int j, bool upd, double* Pl, int64_t ldl, int64_t i0,
+                                    int64_t nloc, double* xs, const double* vs, const double* zk, double* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int j1 = j + 1;
+  const int64_t lb = (j > i0) ? (j - i0) : 0;  // first local row with i >= j
+  {
+    double* p1 = Pl + (int64_t)j1 * ldl;
+    const double z1 = zk[j1];
+    for (int64_t l = tid; l < nloc; l += NT) {
+      double x = p1[l];
+      if (upd && l >= lb) {
+        x = fma(-z1, vs[l], x);
+        p1[l] = x;
+      }
+      xs[l] = (i0 + l >= j1) ? x : 0.0;
+    }
+  }
+  __syncthreads();
+  if (a.staged) {
+    const int slots = a.w - j1;
+    int tps = 1;
+    while (tps * 2 * slots <= NT && tps < 32) tps *= 2;
+    const int k = j1 + tid / tps, sub = tid % tps;
+    double acc = 0.0;
+    if (k < a.w) {
+      if (k == j1) {
+        for (int64_t l = lb + sub; l < nloc; l += tps)
+          if (i0 + l > j1) acc = fma(xs[l], xs[l], acc);
+      } else {
+        double* pk = Pl + (int64_t)k * ldl;
+        const double zz = zk[k];
+        if (upd) {
+          for (int64_t l = lb + sub; l < nloc; l += tps) {
+            const double pv = fma(-zz, vs[l], pk[l]);
+            pk[l] = pv;
+            acc = fma(xs[l], pv, acc);
+          }
+        } else {
+          for (int64_t l = lb + sub; l < nloc; l += tps) acc = fma(xs[l], pk[l], acc);
+        }
+      }
+    }
+    for (int o = tps / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (k < a.w && sub == 0) out[(int64_t)k * a.nb] = acc;
+  } else {
+    for (int k = j1 + warp; k < a.w; k += NT / 32) {
+      double acc = 0.0;
+      if (k == j1) {
+        for (int64_t l = lb + lane; l < nloc; l += 32)
+          if (i0 + l > j1) acc = fma(xs[l], xs[l], acc);
+      } else {
+        double* pk = Pl + (int64_t)k * ldl;
+        const double zz = zk[k];
+        for (int64_t l = lb + lane; l < nloc; l += 32) {
+          double pv = pk[l];
+          if (upd) {
+            pv = fma(-zz, vs[l], pv);
+            pk[l] = pv;
+          }
+          acc = fma(xs[l], pv, acc);
+        }
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) out[(int64_t)k * a.nb] = acc;
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ PanelArgs a) {
   extern __shared__ double smem[];
   __shared__ double red[kMaxW];
@@ -167,21 +244,28 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
     // partial with all its loads in flight, then a fixed 3-step shuffle tree -- deterministic, and one L2
     // round trip per 32 slots instead of one per slot.
     const double* part = a.partials + (int64_t)par * w * a.nb;
+    const double* row = a.rowbuf + (int64_t)par * w;
+    for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);  // P(j, k), in flight with the sums below
     for (int kb = j; kb < w; kb += NT / 8) {
       const int k = kb + (tid >> 3), sub = tid & 7;
       double sum = 0.0;
       if (k < w) {
+        // all of this thread's loads (nb / 8 <= 19) issued before the first add: one L2 round trip
         const double* pk = part + (int64_t)k * a.nb;
-#pragma unroll 4
-        for (int c = sub; c < a.nb; c += 8) sum += __ldcg(pk + c);
+        double v[kMaxLoads];
+#pragma unroll
+        for (int t = 0; t < kMaxLoads; ++t) {
+          const int c = sub + 8 * t;
+          v[t] = c < a.nb ? __ldcg(pk + c) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < kMaxLoads; ++t) sum += v[t];
       }
       sum += __shfl_xor_sync(0xffffffffu, sum, 1);
       sum += __shfl_xor_sync(0xffffffffu, sum, 2);
       sum += __shfl_xor_sync(0xffffffffu, sum, 4);
       if (k < w && sub == 0) red[k] = sum;
     }
-    const double* row = a.rowbuf + (int64_t)par * w;
-    for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);  // P(j, k)
     __syncthreads();
     if (tid == 0) {
       const double sig2 = red[j], alpha = zk[j];
@@ -215,18 +299,11 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
       vs[l] = v;
     }
     __syncthreads();
-    // Trailing update of the panel: P(i, k) -= tau z_k v_i for i >= j, k > j.
-    if (tau != 0.0) {
-      const int64_t lb = (j > i0) ? (j - i0) : 0;
-      for (int k = j + 1 + warp; k < w; k += NT / 32) {
-        double* pk = Pl + (int64_t)k * ldl;
-        const double zz = zk[k];
-        for (int64_t l = lb + lane; l < nloc; l += 32) pk[l] = fma(-zz, vs[l], pk[l]);
-      }
-    }
-    __syncthreads();
     if (j + 1 < w) {
-      column_partials(a, j + 1, Pl, ldl, i0, nloc, xs, a.partials + (int64_t)((j + 1) & 1) * w * a.nb + cta);
+      // Trailing update of the panel (P(i, k) -= tau z_k v_i for i >= j, k > j) with the partial sums of
+      // column j + 1.
+      update_and_partials(a, j, tau != 0.0, Pl, ldl, i0, nloc, xs, vs, zk,
+                          a.partials + (int64_t)((j + 1) & 1) * w * a.nb + cta);
       if ((j + 1) >= i0 && (j + 1) < i1) {
         double* rb = a.rowbuf + (int64_t)((j + 1) & 1) * w;
         const int64_t lj = (j + 1) - i0;
@@ -286,7 +363,7 @@ __global__ void __launch_bounds__(32 * kLarftWarps) larft_kernel(int w, const do
 int choose_nb(int64_t r) {
   const int sms = dev_info().sms;
   int64_t nb = (r + 63) / 64;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(nb, sms));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nb, std::min(sms, kMaxCtas)));
 }
 
 }  // namespace
@@ -361,7 +438,11 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
   if (dyn > kSmemCap) return cudaErrorInvalidValue;
   void* args[] = {(void*)&a};
   count_launch();
+  // profiled work: HQR's 2 r w^2 - 2 w^3 / 3 flops; algorithmic bytes: the panel read and written and Y written
+  cudaEvent_t ev_end = profile_launch_begin(3, 2.0 * r * w * w - 2.0 * w * w * w / 3.0, 0.0, stream,
+                                            24.0 * (double)r * w);
   e = cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(nb), dim3(NT), args, dyn, stream);
+  if (ev_end != nullptr) cudaEventRecord(ev_end, stream);
   if (e != cudaSuccess) return e;
   if (Tf != nullptr) {
     GemmDesc g;

@@ -331,9 +331,9 @@ SideStream* side_stream() {
   return &ss;
 }
 
-// SMs the main stream leaves free while an SVD runs beside it (the 2-CTA cluster and the one-CTA FP32
-// pre-pass, with room for the cluster to find two SMs of one GPC).
-constexpr int kSideReserve = 4;
+// SMs the main stream leaves free while an SVD runs beside it: the 8-CTA cluster (its one-CTA FP32
+// pre-pass runs first, on one of the same SMs).
+constexpr int kSideReserve = 8;
 
 rrf_status check_args(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int q, double* U,
                       int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv, const rrf_opts* opts) {
@@ -586,7 +586,7 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         RRF_CUDA_TRY(cudaEventRecord(side->ev_r[par], s));
         RRF_CUDA_TRY(cudaStreamWaitEvent(side->s, side->ev_r[par], 0));
         RRF_CUDA_TRY(jacobi_svd(b, Rp, b, par ? w.Us1 : w.Us, b, par ? w.sig1 : w.sig, par ? w.Vs1 : w.Vs, b, w.hdr2,
-                                side->s, w.jscr, w.jscr_bytes, true));
+                                side->s, w.jscr, w.jscr_bytes));
         RRF_CUDA_TRY(cudaEventRecord(side->ev_j[par], side->s));
         w.eng.max_ctas = std::max(1, dev_info().sms - kSideReserve);
         pend = {true, i, o, r, c, par};
@@ -606,9 +606,9 @@ extern "C" rrf_status rrf_randutv(int64_t m, int64_t n, const double* A, int64_t
         RRF_CUDA_TRY(gemm_run(w.eng, g3, 2, s));
       }
       if (side == nullptr) {
-        // SVD of R and the small updates, in order.  The same (narrow) SVD kernel as on the side stream, so
-        // both schedules give the same bits.
-        RRF_CUDA_TRY(jacobi_svd(b, Rp, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s, w.gemm, w.gemm_bytes, true));
+        // SVD of R and the small updates, in order.  The same SVD kernel (cluster size and pre-pass) as on
+        // the side stream, so both schedules give the same bits.
+        RRF_CUDA_TRY(jacobi_svd(b, Rp, b, w.Us, b, w.sig, w.Vs, b, w.hdr, s, w.gemm, w.gemm_bytes));
         pend = {true, i, o, r, c, 0};
         RRF_CUDA_TRY(small_updates());
         if (frob_tol > 0.0) RRF_CUDA_TRY(below_tol(i, &stop));

@@ -144,10 +144,9 @@ cudaError_t panel_qr(int64_t r, int64_t w, double* P, int64_t ldp, double* tau, 
 // One-sided Jacobi SVD of a c x c block (c <= 256) on one thread-block cluster.  With scratch of at least
 // jacobi_scratch_bytes(c) (> 0 for 32 <= c <= 256) an FP32 pre-pass supplies the starting V.
 size_t jacobi_scratch_bytes(int64_t c);
-// narrow: use the fewest SMs (a 2-CTA cluster for c <= 128), for an SVD that runs beside other kernels.
 cudaError_t jacobi_svd(int64_t c, const double* M, int64_t ldm, double* Us, int64_t ldu, double* s,
                        double* Vs, int64_t ldv, WsHeader* hdr, cudaStream_t stream, double* scratch = nullptr,
-                       size_t scratch_bytes = 0, bool narrow = false);
+                       size_t scratch_bytes = 0);
 
 // ---- BF16 tensor-core GEMM (gemm_bf16_tc.cu) ------------------------------------------------------
 // D (FP64, M x N, ldd) = alpha * A (M x K) B (N x K)^T, BF16 operands with K contiguous (ld multiple of 8,

@@ -31,7 +31,7 @@ EXPORTED = [
     "rrf_batch_plan_tiles", "rrf_batch_plan_destroy", "rrf_powerurv_batched_f32", "rrf_mlp_param_count",
     "rrf_mlp_train_workspace", "rrf_mlp_forward", "rrf_mlp_grad", "rrf_mlp_adam", "rrf_gemm_emulated_workspace",
     "rrf_gemm_emulated", "rrf_gemm_profile_emulated", "rrf_low_rank_workspace", "rrf_low_rank",
-    "rrf_gemm_profile_bf16", "rrf_test_inject", "rrf_gemm_profile_emulated_bytes",
+    "rrf_gemm_profile_bf16", "rrf_test_inject", "rrf_gemm_profile_emulated_bytes", "rrf_gemm_profile_panel",
 ]
 
 
@@ -156,6 +156,8 @@ def lib():
             L.rrf_low_rank_workspace.restype = _sz
             L.rrf_low_rank.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]
             L.rrf_low_rank.restype = ctypes.c_int
+            L.rrf_gemm_profile_panel.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.POINTER(ctypes.c_int64)]
+            L.rrf_gemm_profile_panel.restype = ctypes.c_int
             L.rrf_gemm_profile_emulated_bytes.argtypes = [ctypes.POINTER(ctypes.c_double)]
             L.rrf_gemm_profile_emulated_bytes.restype = ctypes.c_int
             L.rrf_test_inject.argtypes = [ctypes.c_int, ctypes.c_longlong]
@@ -486,6 +488,14 @@ def gemm_profile_emulated_bytes() -> float:
     if lib().rrf_gemm_profile_emulated_bytes(ctypes.byref(b)) != 0:
         raise RuntimeError("rrf_gemm_profile_emulated_bytes failed")
     return b.value
+
+
+def gemm_profile_panel():
+    """After gemm_profile_end: (device ms, HQR flops, algorithmic bytes, launches) of the panel kernel."""
+    ms, fl, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    if lib().rrf_gemm_profile_panel(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by), ctypes.byref(n)) != 0:
+        raise RuntimeError("rrf_gemm_profile_panel failed")
+    return ms.value, fl.value, by.value, n.value
 
 
 def gemm_profile_bf16():
