@@ -7,7 +7,7 @@
 //     v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta),
 // so one reduction of [sigma^2, x^T P(:, j+1:w)] plus the owner's copy of row j gives every CTA the
 // reflector and all update coefficients.  One grid barrier per column.  Partial sums are combined in
-// a fixed order (per slot: every 8th CTA per thread, then a fixed shuffle tree), so the result is
+// a fixed order (per slot: every 4th CTA per thread, then a fixed shuffle tree), so the result is
 // bitwise deterministic.  Every barrier wait is bounded in time and records RRF_TIMEOUT in the
 // workspace status word instead of hanging.
 //
@@ -24,7 +24,7 @@ constexpr int NT = 256;
 constexpr int kMaxW = 256;
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kMaxCtas = 160;                       // panel CTAs (one per SM at most)
-constexpr int kMaxLoads = kMaxCtas / 8;             // partial sums one thread adds per slot
+constexpr int kTps = 8;                             // threads that share one slot of the partial-sum reduction
 
 struct PanelArgs {
   int64_t r;
@@ -206,6 +206,35 @@ __device__ void update_and_partials(const PanelArgs& a, int j, bool upd, double*
   __syncthreads();
 }
 
+// Sum of the nb CTAs' partials of every slot k in [j, w) into red[k]: kTps threads per slot, each adding
+// every kTps-th CTA's partial (L >= nb / kTps loads, all in flight before the first add), then a fixed
+// shuffle tree -- deterministic, one L2 round trip per NT / kTps slots.  Every CTA computes all slots, so
+// the adds on the FP64 pipe (nb + 2 kTps per slot) are sized exactly: no padding adds.
+template <int L>
+__device__ __forceinline__ void reduce_slots(const double* __restrict__ part, int nb, int j, int w, double* red) {
+  const int tid = threadIdx.x;
+  for (int kb = j; kb < w; kb += NT / kTps) {
+    const int k = kb + tid / kTps, sub = tid % kTps;
+    double sum = 0.0;
+    if (k < w) {
+      const double* pk = part + (int64_t)k * nb;
+      double v[L];
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        const int c = sub + kTps * t;
+        v[t] = c < nb ? __ldcg(pk + c) : 0.0;
+      }
+      sum = v[0];
+#pragma unroll
+      for (int t = 1; t < L; ++t)
+        if (sub + kTps * t < nb) sum += v[t];
+    }
+#pragma unroll
+    for (int o = 1; o < kTps; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (k < w && sub == 0) red[k] = sum;
+  }
+}
+
 __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ PanelArgs a) {
   extern __shared__ double smem[];
   __shared__ double red[kMaxW];
@@ -240,31 +269,21 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
 
   for (int j = 0; j < w; ++j) {
     const int par = j & 1;
-    // Reduce the partial sums: 8 threads per slot (32 slots per pass), each adding every 8th CTA's
-    // partial with all its loads in flight, then a fixed 3-step shuffle tree -- deterministic, and one L2
-    // round trip per 32 slots instead of one per slot.
+    // Reduce the partial sums (the loads of P(j, k) above are in flight with them).
     const double* part = a.partials + (int64_t)par * w * a.nb;
     const double* row = a.rowbuf + (int64_t)par * w;
-    for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);  // P(j, k), in flight with the sums below
-    for (int kb = j; kb < w; kb += NT / 8) {
-      const int k = kb + (tid >> 3), sub = tid & 7;
-      double sum = 0.0;
-      if (k < w) {
-        // all of this thread's loads (nb / 8 <= 19) issued before the first add: one L2 round trip
-        const double* pk = part + (int64_t)k * a.nb;
-        double v[kMaxLoads];
-#pragma unroll
-        for (int t = 0; t < kMaxLoads; ++t) {
-          const int c = sub + 8 * t;
-          v[t] = c < a.nb ? __ldcg(pk + c) : 0.0;
-        }
-#pragma unroll
-        for (int t = 0; t < kMaxLoads; ++t) sum += v[t];
-      }
-      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-      sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-      if (k < w && sub == 0) red[k] = sum;
+    for (int k = j + tid; k < w; k += NT) zk[k] = __ldcg(row + k);
+    switch ((a.nb + 4 * kTps - 1) / (4 * kTps)) {  // loads per thread, rounded up to a multiple of 4
+      case 1: reduce_slots<4>(part, a.nb, j, w, red); break;
+      case 2: reduce_slots<8>(part, a.nb, j, w, red); break;
+      case 3: reduce_slots<12>(part, a.nb, j, w, red); break;
+      case 4: reduce_slots<16>(part, a.nb, j, w, red); break;
+      case 5: reduce_slots<20>(part, a.nb, j, w, red); break;
+      case 6: reduce_slots<24>(part, a.nb, j, w, red); break;
+      case 7: reduce_slots<28>(part, a.nb, j, w, red); break;
+      case 8: reduce_slots<32>(part, a.nb, j, w, red); break;
+      case 9: reduce_slots<36>(part, a.nb, j, w, red); break;
+      default: reduce_slots<40>(part, a.nb, j, w, red); break;
     }
     __syncthreads();
     if (tid == 0) {
@@ -333,36 +352,58 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
 // Columns of the inverse are independent -- Tf(j, j) = tau_j, Tf(i, j) = -tau_i sum_{i<l<=j} S(i, l) Tf(l, j)
 // for i = j-1 .. 0 -- so each column is one warp's back substitution (lanes split the sum, fixed shuffle
 // tree: deterministic), and the w columns run on w / 8 CTAs at once instead of w dependent steps on one.
+// The rows of S a CTA's back substitutions read next are staged in shared memory kLarftRows at a time
+// (coalesced, all loads in flight), so each step waits on shared memory, not on an L2 round trip.
 constexpr int kLarftWarps = 8;
+constexpr int kLarftRows = 12;
 __global__ void __launch_bounds__(32 * kLarftWarps) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
                                                                  const double* __restrict__ tau, double* Tf,
                                                                  int64_t ldt) {
   __shared__ double tcol[kLarftWarps][kMaxW];
+  __shared__ double srow[kLarftRows][kMaxW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * kLarftWarps + warp;
-  if (j >= w) return;
+  const int jmax = min(w, (blockIdx.x + 1) * kLarftWarps) - 1;  // last column of this CTA
+  const bool active = j < w;
   double* t = tcol[warp];
-  const double tj = tau[j];
-  if (lane == 0) t[j] = tj;
+  const double tj = active ? tau[j] : 0.0;
+  if (active && lane == 0) t[j] = tj;
   __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    const double ti = tau[i];
-    double dot = 0.0;
-    if (ti != 0.0 && tj != 0.0) {
-      const double* si = S + (int64_t)i * lds;  // S(l, i) = S(i, l): contiguous in l
-      for (int l = i + 1 + lane; l <= j; l += 32) dot = fma(si[l], t[l], dot);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  for (int ib = jmax; ib > 0; ib -= kLarftRows) {
+    const int ilo = max(0, ib - kLarftRows);
+    // srow[i - ilo][l] = S(l, i) = S(i, l) for ilo <= i < ib, i < l <= jmax
+    const int span = jmax + 1;
+    for (int idx = threadIdx.x; idx < (ib - ilo) * span; idx += 32 * kLarftWarps) {
+      const int ii = idx / span, l = idx - ii * span, i = ilo + ii;
+      if (l > i) srow[ii][l] = S[l + (int64_t)i * lds];
     }
-    if (lane == 0) t[i] = (ti != 0.0 && tj != 0.0) ? -ti * dot : 0.0;
-    __syncwarp();
+    __syncthreads();
+    if (active) {
+      for (int i = min(ib, j) - 1; i >= ilo; --i) {
+        const double ti = tau[i];
+        double dot = 0.0;
+        if (ti != 0.0 && tj != 0.0) {
+          const double* si = srow[i - ilo];
+          for (int l = i + 1 + lane; l <= j; l += 32) dot = fma(si[l], t[l], dot);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        }
+        if (lane == 0) t[i] = (ti != 0.0 && tj != 0.0) ? -ti * dot : 0.0;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
   }
-  for (int i = lane; i < w; i += 32) Tf[i + (int64_t)j * ldt] = (i <= j) ? t[i] : 0.0;
+  if (active)
+    for (int i = lane; i < w; i += 32) Tf[i + (int64_t)j * ldt] = (i <= j) ? t[i] : 0.0;
 }
 
+// CTAs for an r-row panel.  Per column every CTA adds all nb partials of each slot (~nb FP64 adds) and
+// updates its r / nb rows (2 r / nb FMAs) on a narrow FP64 pipe; nb ~ sqrt(2 r) balances the two.
 int choose_nb(int64_t r) {
   const int sms = dev_info().sms;
-  int64_t nb = (r + 63) / 64;
+  int64_t nb = 1;
+  while (nb * nb < 2 * r) ++nb;
   return (int)std::max<int64_t>(1, std::min<int64_t>(nb, std::min(sms, kMaxCtas)));
 }
 
