@@ -74,7 +74,7 @@ __device__ __forceinline__ void round_pair(int t, int k, int ne, int& p, int& q)
 // PRE: FP32 pre-pass for c > 128 -- sweeps on M 2^-e in FP32 (tolerance 2^-16, at most kPreSweeps) and
 // only the accumulated V (as FP64) written to a.Vs; the FP64 sweeps then start from it.
 template <int CL, bool PRE>
-__global__ void __launch_bounds__(NT) jacobi_kernel(const __grid_constant__ JacobiArgs a) {
+__global__ void __launch_bounds__(NT, 1) jacobi_kernel(const __grid_constant__ JacobiArgs a) {
   using T = typename std::conditional<PRE, float, double>::type;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
