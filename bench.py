@@ -27,13 +27,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "factorizations/s (randUTV + powerURV, FP64, 8192^2, b=128, q=1)"
 WORKLOAD = "randUTV_basic + powerURV on 8192x8192 A = Q1 diag(s) Q2^T, s_j = 10^(-8j/n) (j < n/2) then 1e-4"
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of ozaki_gemm_kernel taken from ncu captures
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel, taken from ncu captures
 # summarised under profiles/ (figures copied from those files, not measured by this script).  Each entry
-# names the source of the kernel it was taken on (sha1 of csrc/gemm_ozaki.cu); when that file has changed
+# names the source file of the kernel and its sha1 when the capture was taken; when that file has changed
 # since, the figure no longer describes the kernel and the line reports traffic as null.
-OZAKI_TRAFFIC = {
-    "gemm_4096": {"bytes_per_launch": None, "kernel_sha1": None, "profile": None},
-    "step_8192": {"bytes_per_launch": None, "kernel_sha1": None, "profile": None},
+KERNEL_TRAFFIC = {
+    "ozaki_gemm_4096": {"source": "gemm_ozaki.cu", "bytes_per_launch": 2692.4e6,
+                        "kernel_sha1": "743ee3e3a4983c7b2f3f388799e9409ce849fb71",
+                        "profile": "profiles/ozaki_gemm_kernel_4096.md"},
+    "ozaki_step_8192": {"source": "gemm_ozaki.cu", "bytes_per_launch": 263.5e6,
+                        "kernel_sha1": "743ee3e3a4983c7b2f3f388799e9409ce849fb71",
+                        "profile": "profiles/kernel_dram_8192_step.md"},
+    "panel_step_8192": {"source": "panel_qr.cu", "bytes_per_launch": 4.4e6,
+                        "kernel_sha1": "5a262c90a3c339b5d563644dcc85bd64e3cdfb15",
+                        "profile": "profiles/kernel_dram_8192_step.md"},
 }
 # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (measured 1.19 TFLOP/s at 1995 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -70,19 +77,19 @@ def parse():
     return p.parse_args()
 
 
-def ozaki_sha1() -> str:
+def source_sha1(name: str) -> str:
     import hashlib
-    with open(os.path.join(ROOT, "paper_2106_13402_gb300", "csrc", "gemm_ozaki.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2106_13402_gb300", "csrc", name), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def ozaki_traffic(which: str):
+def kernel_traffic(which: str):
     """(bytes per launch, source) of the recorded ncu capture, or (None, why) when there is none for the
     kernel as it is now."""
-    t = OZAKI_TRAFFIC[which]
+    t = KERNEL_TRAFFIC[which]
     if t["bytes_per_launch"] is None:
         return None, "no capture recorded"
-    if t["kernel_sha1"] != ozaki_sha1():
+    if t["kernel_sha1"] != source_sha1(t["source"]):
         return None, f"kernel changed since {t['profile']}"
     return t["bytes_per_launch"], f"ncu capture, {t['profile']} (copied, not measured here)"
 
@@ -267,7 +274,7 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
         # sustained BF16 peak)
         achieved = emu_tflops / (emu_ms / 1e3) / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
-        traffic, tsrc = ozaki_traffic("step_8192")
+        traffic, tsrc = kernel_traffic("ozaki_step_8192")
         kernels.append((emu_ms, {
             "kernel": "ozaki_gemm_kernel (FP64 product emulated with 7 BF16 digit slices)", "bound": "tensor",
             "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -282,11 +289,12 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
             "share_of_step": round(emu_ms / (ms_step * steps), 4)}))
     if pan_ms > 0:
         achieved = pan_flops / (pan_ms / 1e3) / 1e12
+        ptraffic, ptsrc = kernel_traffic("panel_step_8192")
         kernels.append((pan_ms, {
             "kernel": "panel_qr_kernel (Householder panel, one grid-wide reduction per column)", "bound": "alu",
             "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-            "traffic_source": "no capture of this kernel's DRAM bytes",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": ptraffic, "traffic_source": ptsrc,
+            "traffic_unit": "DRAM bytes read + written per launch, averaged over the launches of one step",
             "work": "HQR flops 2 r w^2 - 2 w^3 / 3 per launch on the FP64 pipe (latency-bound: one grid barrier per column)",
             "algorithmic_bytes_per_launch": round(pan_bytes / max(pan_launches, 1)),
             "achieved_gbs_algorithmic": round(pan_bytes / (pan_ms / 1e3) / 1e9, 1),
@@ -896,8 +904,8 @@ def run_gemm(args):
         "data": "synthetic", "config": {"workload": "C = A B, A and B 4096 x 4096 N(0,1) FP64", "l2": "inputs 256 MB, larger than L2"},
         "clocks": clocks, "gpu_launches": None,
         "roofline": {"kernel": "ozaki_gemm_kernel", "bound": "tensor", "achieved": round(ach, 2), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ozaki_traffic("gemm_4096")[0],
-                     "traffic_source": ozaki_traffic("gemm_4096")[1],
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": kernel_traffic("ozaki_gemm_4096")[0],
+                     "traffic_source": kernel_traffic("ozaki_gemm_4096")[1],
                      "traffic_unit": "bytes per launch (dram read + write, ncu)",
                      "algorithmic_bytes": 2 * 7 * m * k * 2 + 8 * m * n,
                      "peak_source": f"{peak_src} bf16_tflops (burst)", "avg_launch_ms": round(emu_ms / max(emu_launches, 1), 4),
