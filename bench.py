@@ -38,8 +38,8 @@ KERNEL_TRAFFIC = {
     "ozaki_step_8192": {"source": "gemm_ozaki.cu", "bytes_per_launch": 263.5e6,
                         "kernel_sha1": "743ee3e3a4983c7b2f3f388799e9409ce849fb71",
                         "profile": "profiles/kernel_dram_8192_step.md"},
-    "panel_step_8192": {"source": "panel_qr.cu", "bytes_per_launch": 4.44e6,
-                        "kernel_sha1": "21f9e87304b4691c0500b0a9f65f119b5a2a2380",
+    "panel_step_8192": {"source": "panel_qr.cu", "bytes_per_launch": 4.4e6,
+                        "kernel_sha1": "5a262c90a3c339b5d563644dcc85bd64e3cdfb15",
                         "profile": "profiles/kernel_dram_8192_step.md"},
 }
 # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (measured 1.19 TFLOP/s at 1995 MHz).

@@ -351,14 +351,11 @@ __global__ void __launch_bounds__(NT) panel_qr_kernel(const __grid_constant__ Pa
 // identity and drop out: row and column j of Tf are zero, the rest is the inverse on the other indices.
 // Columns of the inverse are independent -- Tf(j, j) = tau_j, Tf(i, j) = -tau_i sum_{i<l<=j} S(i, l) Tf(l, j)
 // for i = j-1 .. 0 -- so each column is one warp's back substitution (lanes split the sum, fixed shuffle
-// tree: deterministic), and the w columns run at once instead of w dependent steps on one.  One warp per
-// CTA: every step is a handful of warp-wide FP64 instructions, each of which holds an SM's narrow FP64
-// pipe for 16 cycles, so columns sharing an SM would wait on each other (eight per CTA measured 0.13 ms
-// per 128-column factor).  The rows of S a column's back substitution reads next are staged in shared
-// memory kLarftRows at a time (coalesced, all loads in flight), so each step waits on shared memory, not
-// on an L2 round trip.
-constexpr int kLarftWarps = 1;
-constexpr int kLarftRows = 16;
+// tree: deterministic), and the w columns run on w / 8 CTAs at once instead of w dependent steps on one.
+// The rows of S a CTA's back substitutions read next are staged in shared memory kLarftRows at a time
+// (coalesced, all loads in flight), so each step waits on shared memory, not on an L2 round trip.
+constexpr int kLarftWarps = 8;
+constexpr int kLarftRows = 12;
 __global__ void __launch_bounds__(32 * kLarftWarps) larft_kernel(int w, const double* __restrict__ S, int64_t lds,
                                                                  const double* __restrict__ tau, double* Tf,
                                                                  int64_t ldt) {
