@@ -97,3 +97,50 @@ def test_input_recipes_have_the_prescribed_spectra():
     assert np.linalg.matrix_rank(A) == 8
     G, none = testmats.make_matrix(30, 20, "gaussian", 3, 4)
     assert none is None and G.flags["F_CONTIGUOUS"]
+
+
+class _FakeProfiler:
+    """Stands in for the library's event-profiler getters (no GPU): fixed per-kind sums."""
+
+    def __init__(self, emu_ms, pan_ms, dfma_ms):
+        self.emu_ms, self.pan_ms, self.dfma_ms = emu_ms, pan_ms, dfma_ms
+
+    def gemm_profile_end(self):
+        return self.dfma_ms, 1e9, 10
+
+    def gemm_profile_emulated(self):
+        return self.emu_ms, 2e12, 56e12, 100
+
+    def gemm_profile_emulated_bytes(self):
+        return 2.0e10
+
+    def gemm_profile_panel(self):
+        return self.pan_ms, 2.6e8 * 30, 1.2e7 * 30, 30
+
+
+PEAKS = {"hbm_gbs": 6674.5, "bf16_tflops": 1903.3, "bf16_tflops_sustained": 1712.4}
+
+
+def test_roofline_reports_the_kernel_with_the_most_time():
+    r = bench.dominant_kernel_roofline(_FakeProfiler(40.0, 50.0, 2.0), 100.0, 1, PEAKS, "measured")
+    assert r["kernel"].startswith("panel_qr_kernel") and r["bound"] == "alu"
+    assert [o["kernel"].split()[0] for o in r["others"]] == ["ozaki_gemm_kernel", "gemm_f64_kernel"]
+    # achieved = flops / time; frac against the FP64 pipe's peak
+    assert abs(r["achieved"] - 2.6e8 * 30 / 0.05 / 1e12) < 1e-3
+    assert abs(r["frac"] - r["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-3
+    r = bench.dominant_kernel_roofline(_FakeProfiler(60.0, 50.0, 2.0), 100.0, 1, PEAKS, "measured")
+    assert r["kernel"].startswith("ozaki_gemm_kernel") and r["bound"] == "tensor"
+    assert abs(r["achieved"] - 56e12 / 0.06 / 1e12) < 1e-2
+    assert r["peak"] == PEAKS["bf16_tflops_sustained"]
+    assert abs(r["share_of_step"] - 0.6) < 1e-9
+
+
+def test_kernel_traffic_is_withdrawn_when_the_source_changes(monkeypatch):
+    entry = dict(bench.KERNEL_TRAFFIC["ozaki_step_8192"])
+    monkeypatch.setitem(bench.KERNEL_TRAFFIC, "probe", dict(entry, kernel_sha1=bench.source_sha1(entry["source"])))
+    assert bench.kernel_traffic("probe")[0] == entry["bytes_per_launch"]
+    monkeypatch.setitem(bench.KERNEL_TRAFFIC, "probe", dict(entry, kernel_sha1="0" * 40))
+    value, why = bench.kernel_traffic("probe")
+    assert value is None and "changed" in why
+    monkeypatch.setitem(bench.KERNEL_TRAFFIC, "probe", dict(entry, bytes_per_launch=None))
+    assert bench.kernel_traffic("probe") == (None, "no capture recorded")
