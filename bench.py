@@ -29,17 +29,18 @@ METRIC = "factorizations/s (randUTV + powerURV, FP64, 8192^2, b=128, q=1)"
 WORKLOAD = "randUTV_basic + powerURV on 8192x8192 A = Q1 diag(s) Q2^T, s_j = 10^(-8j/n) (j < n/2) then 1e-4"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel, taken from ncu captures
 # summarised under profiles/ (figures copied from those files, not measured by this script).  Each entry
-# names the source file of the kernel and its sha1 when the capture was taken; when that file has changed
-# since, the figure no longer describes the kernel and the line reports traffic as null.
+# names the source file of the kernel and the sha1 of its code (source_sha1: comments and blank lines
+# removed) when the capture was taken; when the code has changed since, the figure no longer describes
+# the kernel and the line reports traffic as null.
 KERNEL_TRAFFIC = {
     "ozaki_gemm_4096": {"source": "gemm_ozaki.cu", "bytes_per_launch": 2692.4e6,
-                        "kernel_sha1": "743ee3e3a4983c7b2f3f388799e9409ce849fb71",
+                        "kernel_sha1": "22b0be53d7c17448df989afd2bbd60402a74adf1",
                         "profile": "profiles/ozaki_gemm_kernel_4096.md"},
     "ozaki_step_8192": {"source": "gemm_ozaki.cu", "bytes_per_launch": 263.5e6,
-                        "kernel_sha1": "743ee3e3a4983c7b2f3f388799e9409ce849fb71",
+                        "kernel_sha1": "22b0be53d7c17448df989afd2bbd60402a74adf1",
                         "profile": "profiles/kernel_dram_8192_step.md"},
     "panel_step_8192": {"source": "panel_qr.cu", "bytes_per_launch": 4.4e6,
-                        "kernel_sha1": "5a262c90a3c339b5d563644dcc85bd64e3cdfb15",
+                        "kernel_sha1": "562da21b6e4a15c7f25d40f97605d5b3c9c08b1f",
                         "profile": "profiles/kernel_dram_8192_step.md"},
 }
 # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (measured 1.19 TFLOP/s at 1995 MHz).
@@ -77,10 +78,17 @@ def parse():
     return p.parse_args()
 
 
-def source_sha1(name: str) -> str:
+def source_sha1(name: str, text: str | None = None) -> str:
+    """sha1 of a kernel source's code: comments, trailing blanks and empty lines removed, so that only a
+    change of the code itself withdraws a recorded figure."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2106_13402_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    import re
+    if text is None:
+        with open(os.path.join(ROOT, "paper_2106_13402_gb300", "csrc", name), encoding="utf-8") as f:
+            text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha1("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
 def kernel_traffic(which: str):

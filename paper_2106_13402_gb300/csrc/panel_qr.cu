@@ -7,7 +7,7 @@
 //     v^T P(:, k) = (x^T P(:, k) - beta P(j, k)) / (alpha - beta),
 // so one reduction of [sigma^2, x^T P(:, j+1:w)] plus the owner's copy of row j gives every CTA the
 // reflector and all update coefficients.  One grid barrier per column.  Partial sums are combined in
-// a fixed order (per slot: every 4th CTA per thread, then a fixed shuffle tree), so the result is
+// a fixed order (per slot: every 8th CTA per thread, then a fixed shuffle tree), so the result is
 // bitwise deterministic.  Every barrier wait is bounded in time and records RRF_TIMEOUT in the
 // workspace status word instead of hanging.
 //

@@ -144,3 +144,11 @@ def test_kernel_traffic_is_withdrawn_when_the_source_changes(monkeypatch):
     assert value is None and "changed" in why
     monkeypatch.setitem(bench.KERNEL_TRAFFIC, "probe", dict(entry, bytes_per_launch=None))
     assert bench.kernel_traffic("probe") == (None, "no capture recorded")
+
+
+def test_kernel_code_hash_ignores_comments_only():
+    code = "// header\n__global__ void k(int* p) {  /* body */\n  p[0] = 1;  // store\n}\n"
+    same = "// another header\n\n__global__ void k(int* p) {\n  p[0] = 1;\n}\n"
+    other = "__global__ void k(int* p) {\n  p[0] = 2;\n}\n"
+    assert bench.source_sha1("x", code) == bench.source_sha1("x", same)
+    assert bench.source_sha1("x", code) != bench.source_sha1("x", other)
