@@ -316,6 +316,9 @@ def dominant_kernel_roofline(rrf, ms_step, steps, peaks, peak_src):
             "traffic": None, "peak_source": fp64_src, "launches": int(gemm_launches),
             "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4),
             "share_of_step": round(gemm_ms / (ms_step * steps), 4)}))
+    if not kernels:
+        return {"kernel": None, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "note": "no profiled launch in the pass", "others": []}
     kernels.sort(key=lambda t: -t[0])
     roof = dict(kernels[0][1])
     roof["others"] = [k for _, k in kernels[1:]]

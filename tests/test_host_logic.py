@@ -133,6 +133,8 @@ def test_roofline_reports_the_kernel_with_the_most_time():
     assert abs(r["achieved"] - 56e12 / 0.06 / 1e12) < 1e-2
     assert r["peak"] == PEAKS["bf16_tflops_sustained"]
     assert abs(r["share_of_step"] - 0.6) < 1e-9
+    r = bench.dominant_kernel_roofline(_FakeProfiler(0.0, 0.0, 0.0), 100.0, 1, PEAKS, "measured")
+    assert r["kernel"] is None and r["others"] == []
 
 
 def test_kernel_traffic_is_withdrawn_when_the_source_changes(monkeypatch):
